@@ -251,3 +251,47 @@ def test_spectra_binning():
     expect[19] = wt  # 199
     assert np.allclose(counts * 10.0, expect, rtol=1e-12)
     assert uo[1] == pytest.approx(wt) and uo[0] == 0.0
+
+
+def test_gather_of_linear_fields_is_exact():
+    # linear interpolation reproduces a linear profile exactly, on both the
+    # node grid (Ey, Ez) and the half-node grid (Ex, By, Bz)
+    s = OracleSim(4, 50, 0.9, rr_on=False, source_node=8)
+    nx = s.nx
+    i = np.arange(nx + 1.0)
+    j = np.arange(nx) + 0.5
+    coef = {"Ex": (0.3, 0.011), "Ey": (-2.0, 0.07), "Ez": (1.5, -0.05), "By": (0.7, 0.03), "Bz": (-1.1, 0.02)}
+    lin = lambda k, pos: coef[k][0] + coef[k][1] * pos
+    s.set_fields(lin("Ex", j), lin("Ey", i), lin("Ez", i), lin("By", j), lin("Bz", j))
+    rng = np.random.default_rng(5)
+    n = 40
+    cells = rng.integers(10, 190, n).astype(np.int32)
+    off = rng.random(n)
+    p = rng.normal(size=(n, 3)) * 3
+    s.load_particles(0, cells, off, p[:, 0], p[:, 1], p[:, 2], 1e-6, -1.0, 1.0)
+    s.step(1)
+    got = s.particles(0)
+    for k in range(n):
+        xi = cells[k] + off[k]
+        E = np.array([lin("Ex", xi), lin("Ey", xi), lin("Ez", xi)])
+        B = np.array([0.0, lin("By", xi), lin("Bz", xi)])
+        pn, _, _ = oracle.push(p[k], E, B, qm=-1.0, dt=s.dt, rr=False)
+        assert np.allclose([got["px"][k], got["py"][k], got["pz"][k]], pn, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("Z,A,mass", [(1, 1.0, 1836.15267343), (2, 4.0, 4.0 * 1822.888486209)])
+def test_foil_ion_charge_to_mass(Z, A, mass):
+    # a uniform Ex accelerates every ion of the foil by (Z/m_i) E dt in one step
+    s = OracleSim(4, 50, 0.9, rr_on=False, source_node=8)
+    s.load_foil(1.0, 0.5, 10.0, Z, A, 4, 3)
+    nx = s.nx
+    s.set_fields(np.full(nx, 2.0), np.zeros(nx + 1), np.zeros(nx + 1), np.zeros(nx), np.zeros(nx))
+    s.step(1)
+    ion = s.particles(1)
+    np.testing.assert_allclose(ion["px"], Z / mass * 2.0 * s.dt, rtol=1e-13)
+    el = s.particles(0)
+    np.testing.assert_allclose(el["px"], -2.0 * s.dt, rtol=1e-13)
+    # ion weight: the ions neutralise the electrons, rho = 0 initially
+    pz2 = (Z / mass * 2 * s.dt) ** 2
+    assert s.energy()[2] == pytest.approx(
+        len(ion["px"]) * (10.0 / (Z * 4)) * s.dx * mass * pz2 / (math.sqrt(1 + pz2) + 1), rel=1e-12)
