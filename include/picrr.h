@@ -1,0 +1,188 @@
+/*
+ * picrr — GB300-native (sm_103a) 1D laser-foil particle-in-cell step with
+ * the leapfrog Landau-Lifshitz radiation-reaction pusher of Tamburini et
+ * al., "Radiation Reaction Effects on Radiation Pressure Acceleration"
+ * (arXiv 1008.1685).
+ *
+ * One time step is: linear field gather, Boris push plus the LL
+ * radiation-reaction kick of Sec. 3 (Eqs. f_r, pertfull, estim1,
+ * estimgamma), charge-conserving current deposit, 1D Yee update of Ex, Ey,
+ * Ez, By, Bz with total-field/scattered-field laser injection and Mur
+ * absorbing ends, and a periodic cell sort of the particles.
+ *
+ * Units (Sec. 2, after Eq. 3dLL): time 1/omega, length c/omega, momentum
+ * m_s c of species s, fields m_e omega c/|e|, densities n_c.  One laser
+ * wavelength is 2*pi; dx = 2*pi / cells_per_lambda, dt = cfl * dx.
+ *
+ * Grid: nodes i = 0..Nx at x = i*dx carry Ey, Ez, Jy, Jz; half nodes
+ * j = 0..Nx-1 at (j+1/2)*dx carry Ex, By, Bz, Jx.  E and B are reported at
+ * integer time (B is the time-centred field the particles see); momenta
+ * at half time.
+ *
+ * Conventions for every entry point:
+ *  - Return PIC_OK (0) or a negative pic_status.  A call that fails leaves
+ *    the simulation unchanged, except pic_step_n, which may stop early and
+ *    then reports the steps completed in *steps_done; the state is then
+ *    consistent at that step.  pic_last_error() describes the last failure.
+ *  - All array arguments are HOST pointers owned by the caller; the library
+ *    copies what it needs before returning.  The library owns all device
+ *    memory it allocates and frees it in pic_destroy.
+ *  - A handle may be used by one thread at a time.  The library keeps no
+ *    global mutable state; handles are independent.
+ *  - Call order: pic_create, then any of pic_load_foil / pic_load_particles
+ *    / pic_set_fields / pic_inject_laser (each at most once, and only before
+ *    the first step), then pic_step_n any number of times.  Read-outs are
+ *    allowed at any time.  Other orders return PIC_ERR_STATE.
+ */
+#ifndef PICRR_H
+#define PICRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_sim pic_sim;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_INVALID_ARG = -1,
+    PIC_ERR_STATE = -2,
+    PIC_ERR_OOM = -3,
+    PIC_ERR_CUDA = -4,
+    PIC_ERR_TIMEOUT = -5,
+    PIC_ERR_UNSUPPORTED = -6
+} pic_status;
+
+enum { PIC_LP = 0, PIC_CP = 1 };
+enum { PIC_ENV_SIN2 = 0, PIC_ENV_TRAPEZOID = 1 };
+enum { PIC_ELECTRON = 0, PIC_ION = 1 };
+enum { PIC_EX = 0, PIC_EY = 1, PIC_EZ = 2, PIC_BY = 3, PIC_BZ = 4, PIC_JX = 5, PIC_JY = 6, PIC_JZ = 7 };
+
+/* Run configuration (Sec. 4: 1D box, laser wavelength lambda = 0.8 um). */
+typedef struct {
+    double length_lambda;    /* box length L in wavelengths, > 0 */
+    double cells_per_lambda; /* grid resolution; Nx = round(L * cells_per_lambda) >= 16 */
+    double cfl;              /* dt/dx, 0 < cfl < 1 (a particle moves < 1 cell per step) */
+    double lambda_um;        /* wavelength in micrometres; sets eps = (4/3) pi r_e / lambda */
+    int rr_on;               /* 1: radiation-reaction kick on electrons (Sec. 3); 0: Boris only */
+    int sort_interval;       /* steps between cell sorts, 1..32 (0 selects 8) */
+    uint64_t seed;           /* seed of the foil loader's counter-based generator */
+    int device;              /* CUDA device ordinal */
+    int source_node;         /* node of the laser injection plane, 2..Nx-4 (0 selects 8) */
+    size_t hbm_budget_bytes; /* device memory limit for this handle, 0 = no limit */
+} pic_config;
+
+/* Create a run: allocates the grid (fields, currents) on cfg->device.
+ * *out is set to NULL on error.  PIC_ERR_OOM if the grid exceeds the budget. */
+pic_status pic_create(const pic_config* cfg, pic_sim** out);
+
+/* Launch all work of this handle on the given cudaStream_t (NULL restores
+ * the handle's own stream).  The stream must belong to the handle's device
+ * and outlive its use.  Host calls still synchronise before returning. */
+pic_status pic_set_stream(pic_sim* sim, void* cuda_stream);
+
+/* Uniform foil of both species (Sec. 4): electrons (charge -1, mass m_e)
+ * and ions of charge ion_Z and mass number ion_A (Z = A = 1: protons,
+ * m_p = 1836.15267343 m_e; otherwise A * 1822.888486209 m_e), density
+ * ne_over_nc electrons per n_c, occupying [x0, x0 + thickness] (in
+ * wavelengths, rounded to whole cells), ppc macro-particles per cell per
+ * species, cold.  Quiet start: electron k and ion k of a cell share the
+ * in-cell offset u = (SplitMix64(seed, cell*ppc + k + 1) >> 40) * 2^-24.
+ * Weights: ne/ppc (electrons), ne/(Z*ppc) (ions). */
+pic_status pic_load_foil(pic_sim* sim, double x0_lambda, double thickness_lambda, double ne_over_nc,
+                         int ion_Z, double ion_A, int ppc);
+
+/* Explicit particles of one species (test and restart path).  cell[n] in
+ * [0, Nx), off[n] in [0,1) is the in-cell offset, px/py/pz in m_s c; all
+ * are rounded to float.  weight: density per macro-particle (n_c); charge
+ * in e; mass in m_e.  Species PIC_ELECTRON gets the radiation-reaction
+ * kick when rr_on is set.  n <= 2^31 - 1. */
+pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_t* cell,
+                              const double* off, const double* px, const double* py,
+                              const double* pz, double weight, double charge, double mass);
+
+/* Initial fields (default all zero): Ey, Ez on Nx+1 nodes; Ex, By, Bz on Nx
+ * half nodes; B at the same integer time as E.  Any pointer may be NULL
+ * (that component stays zero). */
+pic_status pic_set_fields(pic_sim* sim, const double* Ex, const double* Ey, const double* Ez,
+                          const double* By, const double* Bz);
+
+/* Laser entering at the source node, travelling towards +x (Sec. 4).
+ * a0 labels the intensity with the LP convention (I lambda^2 =
+ * 1.37e18 a0^2 W cm^-2 um^2), so CP has a0/sqrt2 per component.
+ * LP: Ey = Bz = a0 g(s) sin(s); CP: Ey = Bz = a0/sqrt2 g sin(s),
+ * Ez = -By = -a0/sqrt2 g cos(s); s = t - (x - x_source).
+ * PIC_ENV_SIN2: g = sin^2(pi s / tau), tau = duration_periods * 2 pi.
+ * PIC_ENV_TRAPEZOID: sin^2 rise and fall of rise_periods each, flat
+ * between, total duration_periods (the shape of Sec. 4). */
+pic_status pic_inject_laser(pic_sim* sim, double a0, int polarization, int envelope,
+                            double duration_periods, double rise_periods);
+
+/* Advance n >= 0 steps.  Synchronous: returns after the device has
+ * finished; *steps_done (nullable) receives the steps completed in this
+ * call.  PIC_ERR_TIMEOUT if a bounded device wait gave up (the state is
+ * then that of the last completed step). */
+pic_status pic_step_n(pic_sim* sim, int64_t n, int64_t* steps_done);
+
+/* Kinetic-energy spectrum of one species, E = m_s c^2 (gamma - 1) in MeV,
+ * nbins linear bins over [e_min, e_max): counts[k] = sum of w*dx over
+ * particles in bin k divided by the bin width (dN/dE per unit area, in
+ * n_c c/omega per MeV).  Particles that left the box are included.
+ * radiated_J_per_m2 (nullable) receives the energy removed by radiation
+ * reaction so far, in J per m^2 of transverse area. */
+pic_status pic_spectra(pic_sim* sim, int species, int nbins, double e_min_MeV, double e_max_MeV,
+                       double* counts, double* radiated_J_per_m2);
+
+/* out[6], energies per unit area in m_e c^2 n_c c/omega (FP64):
+ *  [0] field energy of the accounting region (nodes source+1..Nx-1; B
+ *      enters as B^{n-1/2}.B^{n+1/2}, the quantity the Yee scheme conserves),
+ *  [1] electron kinetic energy, [2] ion kinetic energy (momenta at n-1/2),
+ *  [3] energy radiated by the kick so far, w*dx*(gamma(p_L) - gamma(p)),
+ *  [4] net Poynting flux in through the left accounting plane so far,
+ *  [5] Poynting flux out through the right accounting plane so far. */
+pic_status pic_energy(pic_sim* sim, double out[6]);
+
+/* Particle read-back in load order.  x in c/omega, momenta in m_s c,
+ * flag 0 active, -1 / +1 frozen at x = 0 / x = L.  Arrays (each nullable)
+ * hold at least cap entries; *n (nullable) receives the species count. */
+pic_status pic_read_particles(pic_sim* sim, int species, int64_t cap, double* x, double* px,
+                              double* py, double* pz, int32_t* flag, int64_t* n);
+
+/* One grid component (PIC_EX..PIC_JZ; J of the last step): Nx+1 node values
+ * or Nx half-node values; *n (nullable) receives the count. */
+pic_status pic_read_fields(pic_sim* sim, int comp, int64_t cap, double* out, int64_t* n);
+
+typedef struct {
+    int64_t steps;            /* steps completed since creation */
+    int64_t kernel_launches;  /* device kernels launched by this handle */
+    int64_t push_launches;    /* launches of the fused gather/push/deposit kernel */
+    int64_t sort_count;       /* cell sorts performed */
+    int64_t active_particles; /* particles not frozen at a wall, both species */
+    double push_ms;           /* summed device time of the push kernel (timing on) */
+    double field_ms;          /* summed device time of the Yee kernel (timing on) */
+    double sort_ms;           /* summed device time of the sort kernels (timing on) */
+    int64_t timed_push_launches; /* push launches covered by push_ms */
+    int64_t device_bytes;     /* device memory held by the handle */
+    int32_t n_units;          /* current work units (sorted particle chunks) */
+    int32_t fp_bits;          /* fixed-point fraction bits of the current accumulators */
+} pic_stats_t;
+
+/* Counters and, when timing is on, CUDA-event times of each kernel class,
+ * recorded on the launching stream. */
+pic_status pic_stats(pic_sim* sim, pic_stats_t* out);
+pic_status pic_set_timing(pic_sim* sim, int on);
+
+/* Message for the last failed call on sim (or on creation when sim is NULL,
+ * for the calling thread).  Valid until the next call on the handle. */
+const char* pic_last_error(const pic_sim* sim);
+
+/* Free everything; NULL is accepted. */
+pic_status pic_destroy(pic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

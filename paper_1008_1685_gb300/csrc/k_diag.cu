@@ -1,0 +1,142 @@
+// Diagnostics: field and kinetic energy (FP64 accumulation, fixed-order
+// reductions so repeated calls give identical bits) and the kinetic-energy
+// spectrum (integer bin counts).
+#include "picrr_internal.cuh"
+
+namespace picrr {
+
+namespace {
+
+constexpr int DIAG_T = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sred) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < DIAG_T / 32; ++w) t += sred[w];
+    return t;
+}
+
+// Field energy of the accounting region at integer time n: nodes
+// [is+1, Nx-1] carry (Ey^2 + Ez^2)/2; half nodes [is+1, Nx-2] carry
+// (B^{n-1/2}.B^{n+1/2})/2 = ((B^n)^2 - ((dt/2) curl E^n)^2)/2; all half nodes
+// carry Ex^2/2.  Times dx on the host.
+__global__ void __launch_bounds__(DIAG_T) k_field_energy(const DiagParams D, double* partials) {
+    __shared__ double sred[DIAG_T / 32];
+    const int a = D.is + 1, b = D.Nx - 1;
+    double w = 0.0;
+    for (int i = blockIdx.x * DIAG_T + threadIdx.x; i <= D.Nx; i += gridDim.x * DIAG_T) {
+        const int p = i + PADF;
+        if (i >= a && i <= b) {
+            const double ey = D.F[1][p], ez = D.F[2][p];
+            w += 0.5 * (ey * ey + ez * ez);
+        }
+        if (i >= a && i <= b - 1) {
+            const double by = D.F[3][p], bz = D.F[4][p];
+            const double dy = static_cast<double>(D.hc) * (static_cast<double>(D.F[2][p + 1]) - D.F[2][p]);
+            const double dz = static_cast<double>(D.hc) * (static_cast<double>(D.F[1][p + 1]) - D.F[1][p]);
+            w += 0.5 * (by * by - dy * dy + bz * bz - dz * dz);
+        }
+        if (i < D.Nx) {
+            const double ex = D.F[0][p];
+            w += 0.5 * ex * ex;
+        }
+    }
+    const double t = block_sum(w, sred);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// Sum of (gamma - 1) over all particles of a species (frozen ones included).
+__global__ void __launch_bounds__(DIAG_T) k_kinetic(DevSpecies sp, int64_t n, double* partials) {
+    __shared__ double sred[DIAG_T / 32];
+    double w = 0.0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * DIAG_T + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * DIAG_T) {
+        const double px = sp.px[i], py = sp.py[i], pz = sp.pz[i];
+        const double p2 = px * px + py * py + pz * pz;
+        w += p2 / (sqrt(1.0 + p2) + 1.0);
+    }
+    const double t = block_sum(w, sred);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_reduce(const double* partials, int n, double scale, double* out) {
+    __shared__ double sred[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) v += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 32; ++w) t += sred[w];
+        *out = t * scale;
+    }
+}
+
+// bins[0..nbins) counts, bins[nbins] underflow, bins[nbins+1] overflow.
+// Energy m c^2 (gamma - 1) in MeV evaluated in double.
+__global__ void __launch_bounds__(DIAG_T) k_spectrum(DevSpecies sp, int64_t n, double mass_mev, int nbins,
+                                                     double e_min, double e_max, unsigned long long* bins) {
+    extern __shared__ unsigned int sh[];
+    const bool use_sh = nbins + 2 <= 8192;
+    if (use_sh)
+        for (int i = threadIdx.x; i < nbins + 2; i += DIAG_T) sh[i] = 0u;
+    __syncthreads();
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * DIAG_T + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * DIAG_T) {
+        const double px = sp.px[i], py = sp.py[i], pz = sp.pz[i];
+        const double p2 = px * px + py * py + pz * pz;
+        const double e = mass_mev * p2 / (sqrt(1.0 + p2) + 1.0);
+        int k;
+        if (e < e_min) {
+            k = nbins;
+        } else {
+            const double kf = floor((e - e_min) / (e_max - e_min) * static_cast<double>(nbins));
+            k = kf >= static_cast<double>(nbins) ? nbins + 1 : static_cast<int>(kf);
+        }
+        if (use_sh) atomicAdd(&sh[k], 1u);
+        else atomicAdd(&bins[k], 1ull);
+    }
+    __syncthreads();
+    if (use_sh)
+        for (int i = threadIdx.x; i < nbins + 2; i += DIAG_T)
+            if (sh[i]) atomicAdd(&bins[i], static_cast<unsigned long long>(sh[i]));
+}
+
+}  // namespace
+
+int launch_field_energy(const DiagParams& D, double* partials, int max_blocks, cudaStream_t st) {
+    int g = (D.Nx + 1 + DIAG_T - 1) / DIAG_T;
+    if (g > max_blocks) g = max_blocks;
+    if (g < 1) g = 1;
+    k_field_energy<<<g, DIAG_T, 0, st>>>(D, partials);
+    return g;
+}
+
+int launch_kinetic(DevSpecies sp, int64_t n, double* partials, int max_blocks, cudaStream_t st) {
+    int64_t g = (n + DIAG_T - 1) / DIAG_T;
+    if (g > max_blocks) g = max_blocks;
+    if (g < 1) g = 1;
+    k_kinetic<<<static_cast<int>(g), DIAG_T, 0, st>>>(sp, n, partials);
+    return static_cast<int>(g);
+}
+
+void launch_reduce_partials(const double* partials, int n, double scale, double* out, cudaStream_t st) {
+    k_reduce<<<1, 1024, 0, st>>>(partials, n, scale, out);
+}
+
+void launch_spectrum(DevSpecies sp, int64_t n, double mass_mev, int nbins, double e_min, double e_max,
+                     unsigned long long* bins, cudaStream_t st) {
+    int64_t g = (n + DIAG_T - 1) / DIAG_T;
+    if (g > 1216) g = 1216;
+    if (g < 1) g = 1;
+    const size_t sh = (nbins + 2 <= 8192) ? sizeof(unsigned int) * (nbins + 2) : 0;
+    k_spectrum<<<static_cast<int>(g), DIAG_T, sh, st>>>(sp, n, mass_mev, nbins, e_min, e_max, bins);
+}
+
+}  // namespace picrr

@@ -1,0 +1,315 @@
+// Fused field gather + Boris push + Landau-Lifshitz radiation-reaction kick
+// + move + charge-conserving deposit (the particle part of one PIC step).
+//
+// One CTA per work unit (<= UNIT_P consecutive particles of one species
+// whose cells at the last sort lie in one tile).  Because cfl < 1 a particle
+// moves less than one cell per step, so k steps after the sort every
+// particle of the unit lies in [lo - k, hi + k]; the CTA stages the fields of
+// the window [lo - k - 1, hi + k + 2] into shared memory with one bulk TMA
+// copy per component and accumulates the unit's current there.
+//
+// Determinism: each particle's current is split into at most two "bin"
+// records (its old cell and, if it crossed a boundary, its new cell), each
+// with five values (Jy and Jz shares of the bin's two nodes, and the Jx of
+// the bin's half node).  Warps sum runs of equal bins with a fixed-order
+// segmented shuffle reduction, convert the run sums to 64-bit fixed point
+// and add them with integer atomics, first into shared memory, then into the
+// global accumulators.  Integer addition is associative, so the result does
+// not depend on the order in which warps or CTAs arrive.
+#include "picrr_internal.cuh"
+
+namespace picrr {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Sum runs of equal keys (in lane order) and add each run's total, scaled to
+// fixed point, to sJ[q][key].  key < 0 marks an empty record.
+__device__ __forceinline__ void seg_add(int key, float v0, float v1, float v2, float v3, float v4,
+                                        unsigned long long (*sJ)[WMAX], float scale) {
+    const int lane = threadIdx.x & 31;
+    const int kprev = __shfl_up_sync(FULL, key, 1);
+    const bool head = (lane == 0) || (kprev != key);
+    const unsigned hm = __ballot_sync(FULL, head);
+    const int seg0 = 31 - __clz(hm & (FULL >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t0 = __shfl_up_sync(FULL, v0, o);
+        const float t1 = __shfl_up_sync(FULL, v1, o);
+        const float t2 = __shfl_up_sync(FULL, v2, o);
+        const float t3 = __shfl_up_sync(FULL, v3, o);
+        const float t4 = __shfl_up_sync(FULL, v4, o);
+        if (lane - o >= seg0) {
+            v0 += t0;
+            v1 += t1;
+            v2 += t2;
+            v3 += t3;
+            v4 += t4;
+        }
+    }
+    const bool tail = ((hm >> 1) | 0x80000000u) >> lane & 1u;
+    if (tail && key >= 0) {
+        if (v0 != 0.f) atomicAdd(&sJ[0][key], static_cast<unsigned long long>(__float2ll_rn(v0 * scale)));
+        if (v1 != 0.f) atomicAdd(&sJ[1][key], static_cast<unsigned long long>(__float2ll_rn(v1 * scale)));
+        if (v2 != 0.f) atomicAdd(&sJ[2][key], static_cast<unsigned long long>(__float2ll_rn(v2 * scale)));
+        if (v3 != 0.f) atomicAdd(&sJ[3][key], static_cast<unsigned long long>(__float2ll_rn(v3 * scale)));
+        if (v4 != 0.f) atomicAdd(&sJ[4][key], static_cast<unsigned long long>(__float2ll_rn(v4 * scale)));
+    }
+}
+
+__device__ __forceinline__ int comp(const int4& a, int j) { return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w; }
+__device__ __forceinline__ float comp(const float4& a, int j) {
+    return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
+}
+
+__global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
+    __shared__ __align__(128) float sF[5][WMAX];
+    __shared__ __align__(16) unsigned long long sJ[NQ][WMAX];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double sred[PUSH_T / 32];
+
+    const int u = blockIdx.x;
+    if (u >= P.units.count[0]) return;  // block-uniform
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = P.units.species[u];
+    const int start = P.units.start[u], end = P.units.end[u];
+    const int lo = P.units.lo[u], hi = P.units.hi[u];
+    const int k = P.k;
+    const int w0 = lo - k - 1, w1 = hi + k + 3;
+    const int p0 = (w0 + PADF) & ~3;
+    const int p1 = (w1 + PADF + 3) & ~3;
+    const int L = p1 - p0;
+    if (L > WMAX || p0 < 0) {  // cannot happen for a valid unit table; never index out of the window
+        if (tid == 0) atomicOr(P.status, ST_WINDOW);
+        return;
+    }
+
+    for (int i = tid; i < NQ * WMAX; i += PUSH_T) (&sJ[0][0])[i] = 0ull;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], P.F[c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
+    }
+
+    const DevSpecies sp = P.sp[s];
+    const float qm = P.qm[s], qw = P.qw[s];
+    const float cfl = P.cfl, dt = P.dt, eps = P.eps, scale = P.fp_scale;
+    const bool rr = P.rr[s] != 0;
+    const float hq = 0.5f * qm * dt;
+    const float jxf = qw / cfl;  // q w dx / dt
+    const int base = start & ~3;
+    const int nslots = (end - base + 3) >> 2;
+    const int rounds = (nslots + PUSH_T - 1) / PUSH_T;
+
+    const bool got = mbar_wait_bounded(&bar, 0);
+    if (!__syncthreads_and(got)) {
+        if (tid == 0) {
+            atomicOr(P.status, ST_TIMEOUT);
+            mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
+        }
+        return;
+    }
+
+    float rad = 0.f;
+    for (int r = 0; r < rounds; ++r) {
+        const int slot = r * PUSH_T + tid;
+        const int b4 = base + 4 * slot;
+        const bool slot_ok = slot < nslots;
+        int4 c4 = make_int4(-1, -1, -1, -1);
+        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = o4, y4 = o4, z4 = o4;
+        if (slot_ok) {
+            c4 = __ldcs(reinterpret_cast<const int4*>(sp.cell + b4));
+            o4 = __ldcs(reinterpret_cast<const float4*>(sp.off + b4));
+            x4 = __ldcs(reinterpret_cast<const float4*>(sp.px + b4));
+            y4 = __ldcs(reinterpret_cast<const float4*>(sp.py + b4));
+            z4 = __ldcs(reinterpret_cast<const float4*>(sp.pz + b4));
+        }
+        int cn[4];
+        float fo[4], qx[4], qy[4], qz[4];
+        bool act[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int idx = b4 + j;
+            int c = comp(c4, j);
+            float f = comp(o4, j);
+            float px = comp(x4, j), py = comp(y4, j), pz = comp(z4, j);
+            const int lb = c + PADF - p0;  // local bin of the particle's cell
+            bool a = slot_ok && idx >= start && idx < end && c >= 0;
+            if (a && (lb < 1 || lb > L - 3)) {  // outside the window: leave it, report
+                atomicOr(P.status, ST_WINDOW);
+                a = false;
+            }
+            int ko = -1, kn = -1;
+            float vo0 = 0.f, vo1 = 0.f, vo2 = 0.f, vo3 = 0.f, vo4 = 0.f;
+            float vn0 = 0.f, vn1 = 0.f, vn2 = 0.f, vn3 = 0.f, vn4 = 0.f;
+            if (a) {
+                // --- linear gather: nodes (Ey, Ez) and half nodes (Ex, By, Bz)
+                const float e_y = (1.f - f) * sF[1][lb] + f * sF[1][lb + 1];
+                const float e_z = (1.f - f) * sF[2][lb] + f * sF[2][lb + 1];
+                const float h = f - 0.5f;
+                const int jb = h < 0.f ? lb - 1 : lb;
+                const float g = h < 0.f ? h + 1.f : h;
+                const float e_x = (1.f - g) * sF[0][jb] + g * sF[0][jb + 1];
+                const float b_y = (1.f - g) * sF[3][jb] + g * sF[3][jb + 1];
+                const float b_z = (1.f - g) * sF[4][jb] + g * sF[4][jb + 1];
+                // --- Boris step for the Lorentz force (Bx = 0 in 1D)
+                const float mx = px + hq * e_x, my = py + hq * e_y, mz = pz + hq * e_z;
+                const float ig = 1.f / sqrtf(1.f + mx * mx + my * my + mz * mz);
+                const float ty = hq * b_y * ig, tz = hq * b_z * ig;
+                const float sf = 2.f / (1.f + ty * ty + tz * tz);
+                const float sy = sf * ty, sz = sf * tz;
+                const float ux = mx + my * tz - mz * ty;
+                const float uy = my - mx * tz;
+                const float uz = mz + mx * ty;
+                const float lx = mx + uy * sz - uz * sy + hq * e_x;
+                const float ly = my - ux * sz + hq * e_y;
+                const float lz = mz + ux * sy + hq * e_z;
+                if (rr) {
+                    // --- Eqs. (estim1, estimgamma): p(n) from p_L and p^{n-1/2}
+                    const float bx_ = 0.5f * (lx + px), by_ = 0.5f * (ly + py), bz_ = 0.5f * (lz + pz);
+                    const float igb = 1.f / sqrtf(1.f + bx_ * bx_ + by_ * by_ + bz_ * bz_);
+                    const float vx = bx_ * igb, vy = by_ * igb, vz = bz_ * igb;
+                    // f_L = -(E + v x B)
+                    const float fx = -(e_x + vy * b_z - vz * b_y);
+                    const float fy = -(e_y - vx * b_z);
+                    const float fz = -(e_z + vx * b_y);
+                    const float av = vx * e_x + vy * e_y + vz * e_z;  // v.E = -v.f_L
+                    // gamma^2 [f_L^2 - (v.E)^2] = f_L^2 + |p(n) x f_L|^2 (Lagrange identity),
+                    // a sum of squares: no cancellation in single precision
+                    const float cx = by_ * fz - bz_ * fy, cy = bz_ * fx - bx_ * fz, cz = bx_ * fy - by_ * fx;
+                    const float br = fx * fx + fy * fy + fz * fz + cx * cx + cy * cy + cz * cz;
+                    // Eq. (f_r) and Eq. (pertfull): p^{n+1/2} = p_L + dt f_R
+                    const float kx = -eps * dt * (fy * b_z - fz * b_y - av * e_x + br * vx);
+                    const float ky = -eps * dt * (-fx * b_z - av * e_y + br * vy);
+                    const float kz = -eps * dt * (fx * b_y - av * e_z + br * vz);
+                    px = lx + kx;
+                    py = ly + ky;
+                    pz = lz + kz;
+                    // gamma(p_L) - gamma(p^{n+1/2}) without cancellation
+                    const float gL = sqrtf(1.f + lx * lx + ly * ly + lz * lz);
+                    const float gN = sqrtf(1.f + px * px + py * py + pz * pz);
+                    rad -= (kx * (lx + px) + ky * (ly + py) + kz * (lz + pz)) / (gL + gN);
+                } else {
+                    px = lx;
+                    py = ly;
+                    pz = lz;
+                }
+                // --- move: x^{n+1} = x^n + dt p_x / gamma, in cell units
+                const float ign = 1.f / sqrtf(1.f + px * px + py * py + pz * pz);
+                const float vxn = px * ign, vyn = py * ign, vzn = pz * ign;
+                float fn = f + cfl * vxn;
+                int d = 0;
+                if (fn >= 1.f) {
+                    fn -= 1.f;
+                    d = 1;
+                } else if (fn < 0.f) {
+                    fn += 1.f;
+                    d = -1;
+                    if (fn >= 1.f) {  // rounded up to the boundary: same point as (c, 0)
+                        fn = 0.f;
+                        d = 0;
+                    }
+                }
+                int cnew = c + d, store_c = cnew;
+                if (cnew < 0) {  // frozen at x = 0
+                    cnew = 0;
+                    fn = 0.f;
+                    d = 0;
+                    store_c = -1;
+                } else if (cnew >= P.Nx) {  // frozen at x = L
+                    cnew = P.Nx;
+                    fn = 0.f;
+                    store_c = -2;
+                }
+                // --- deposit records (old bin lb, new bin lb + d)
+                const float ay = 0.5f * qw * vyn, az = 0.5f * qw * vzn;
+                ko = lb;
+                if (d == 0) {
+                    vo0 = ay * ((1.f - f) + (1.f - fn));
+                    vo1 = ay * (f + fn);
+                    vo2 = az * ((1.f - f) + (1.f - fn));
+                    vo3 = az * (f + fn);
+                    vo4 = jxf * (fn - f);
+                } else {
+                    kn = lb + d;
+                    vo0 = ay * (1.f - f);
+                    vo1 = ay * f;
+                    vo2 = az * (1.f - f);
+                    vo3 = az * f;
+                    vo4 = d > 0 ? jxf * (1.f - f) : -jxf * f;
+                    vn0 = ay * (1.f - fn);
+                    vn1 = ay * fn;
+                    vn2 = az * (1.f - fn);
+                    vn3 = az * fn;
+                    vn4 = d > 0 ? jxf * fn : -jxf * (1.f - fn);
+                }
+                c = store_c;
+                f = fn;
+            }
+            seg_add(ko, vo0, vo1, vo2, vo3, vo4, sJ, scale);
+            if (__any_sync(FULL, kn >= 0)) seg_add(kn, vn0, vn1, vn2, vn3, vn4, sJ, scale);
+            act[j] = a;
+            cn[j] = c;
+            fo[j] = f;
+            qx[j] = px;
+            qy[j] = py;
+            qz[j] = pz;
+        }
+        if (slot_ok) {
+            if (b4 >= start && b4 + 3 < end) {
+                __stcs(reinterpret_cast<int4*>(sp.cell + b4), make_int4(cn[0], cn[1], cn[2], cn[3]));
+                __stcs(reinterpret_cast<float4*>(sp.off + b4), make_float4(fo[0], fo[1], fo[2], fo[3]));
+                __stcs(reinterpret_cast<float4*>(sp.px + b4), make_float4(qx[0], qx[1], qx[2], qx[3]));
+                __stcs(reinterpret_cast<float4*>(sp.py + b4), make_float4(qy[0], qy[1], qy[2], qy[3]));
+                __stcs(reinterpret_cast<float4*>(sp.pz + b4), make_float4(qz[0], qz[1], qz[2], qz[3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (!act[j]) continue;
+                    sp.cell[b4 + j] = cn[j];
+                    sp.off[b4 + j] = fo[j];
+                    sp.px[b4 + j] = qx[j];
+                    sp.py[b4 + j] = qy[j];
+                    sp.pz[b4 + j] = qz[j];
+                }
+            }
+        }
+    }
+
+    // radiated energy of the unit: fixed-order block reduction in double
+    double rd = static_cast<double>(rad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rd += __shfl_xor_sync(FULL, rd, o);
+    if (lane == 0) sred[warp] = rd;
+    __syncthreads();  // also orders every shared-memory current update before the flush
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < PUSH_T / 32; ++w) t += sred[w];
+        P.rad_part[u] = t * static_cast<double>(P.rad_w[s]);
+    }
+    // flush the window: node n gets jy_lo of bin n and jy_hi of bin n-1
+    for (int i = tid; i < L; i += PUSH_T) {
+        const unsigned long long jy = sJ[0][i] + (i > 0 ? sJ[1][i - 1] : 0ull);
+        const unsigned long long jz = sJ[2][i] + (i > 0 ? sJ[3][i - 1] : 0ull);
+        const unsigned long long jx = sJ[4][i];
+        if (jx) atomicAdd(P.J[0] + p0 + i, jx);
+        if (jy) atomicAdd(P.J[1] + p0 + i, jy);
+        if (jz) atomicAdd(P.J[2] + p0 + i, jz);
+    }
+}
+
+}  // namespace
+
+void launch_push(const PushParams& P, int grid, cudaStream_t st) {
+    if (grid <= 0) return;
+    k_push_deposit<<<grid, PUSH_T, 0, st>>>(P);
+}
+
+}  // namespace picrr
