@@ -104,6 +104,15 @@ pic_status pic_load_particles(pic_sim* sim, int species, int64_t n, const int32_
                               const double* off, const double* px, const double* py,
                               const double* pz, double weight, double charge, double mass);
 
+/* Same as pic_load_particles with single-precision host arrays, copied as
+ * they are (no conversion).  When cell[] is already non-decreasing the five
+ * arrays go straight to the device with asynchronous copies (pin them for
+ * full bandwidth) and ids are generated on the device; otherwise the library
+ * first makes a cell-ordered host copy. */
+pic_status pic_load_particles_f32(pic_sim* sim, int species, int64_t n, const int32_t* cell,
+                                  const float* off, const float* px, const float* py, const float* pz,
+                                  double weight, double charge, double mass);
+
 /* Initial fields (default all zero): Ey, Ez on Nx+1 nodes; Ex, By, Bz on Nx
  * half nodes; B at the same integer time as E.  Any pointer may be NULL
  * (that component stays zero). */

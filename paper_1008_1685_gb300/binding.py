@@ -22,7 +22,8 @@ STATUS = {0: "PIC_OK", -1: "PIC_ERR_INVALID_ARG", -2: "PIC_ERR_STATE", -3: "PIC_
           -4: "PIC_ERR_CUDA", -5: "PIC_ERR_TIMEOUT", -6: "PIC_ERR_UNSUPPORTED"}
 
 # exported symbols of include/picrr.h
-SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles", "pic_set_fields",
+SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles", "pic_load_particles_f32",
+           "pic_set_fields",
            "pic_inject_laser", "pic_step_n", "pic_spectra", "pic_energy", "pic_read_particles",
            "pic_read_fields", "pic_stats", "pic_set_timing", "pic_last_error", "pic_destroy")
 
@@ -89,6 +90,9 @@ def library():
         L.pic_load_foil.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int]
         L.pic_load_particles.argtypes = [vp, C.c_int, i64, C.POINTER(C.c_int32), dp, dp, dp, dp,
                                          C.c_double, C.c_double, C.c_double]
+        fp = C.POINTER(C.c_float)
+        L.pic_load_particles_f32.argtypes = [vp, C.c_int, i64, C.POINTER(C.c_int32), fp, fp, fp, fp,
+                                             C.c_double, C.c_double, C.c_double]
         L.pic_set_fields.argtypes = [vp, dp, dp, dp, dp, dp]
         L.pic_inject_laser.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double]
         L.pic_step_n.argtypes = [vp, i64, C.POINTER(i64)]
@@ -169,6 +173,15 @@ class Sim:
         self._check(self._L.pic_load_particles(
             self._h, species, len(cell), cell.ctypes.data_as(C.POINTER(C.c_int32)), _dp(off), _dp(px),
             _dp(py), _dp(pz), weight, charge, mass))
+
+    def load_particles_f32(self, species, cell, off, px, py, pz, weight, charge, mass):
+        """Single-precision host arrays (numpy float32 / int32, pinned or not) copied as they are."""
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (off, px, py, pz)]
+        fpp = C.POINTER(C.c_float)
+        self._check(self._L.pic_load_particles_f32(
+            self._h, species, len(cell), cell.ctypes.data_as(C.POINTER(C.c_int32)),
+            *[a.ctypes.data_as(fpp) for a in arrs], weight, charge, mass))
 
     def set_fields(self, Ex=None, Ey=None, Ez=None, By=None, Bz=None):
         arrs = [_f64(a) for a in (Ex, Ey, Ez, By, Bz)]

@@ -382,6 +382,19 @@ __global__ void k_foil(DevSpecies e, DevSpecies ion, int c0, int ncell, int ppc,
 }
 }  // namespace
 
+namespace {
+__global__ void k_iota(int32_t* id, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        id[i] = static_cast<int32_t>(i);
+}
+}  // namespace
+
+void launch_iota(int32_t* id, int64_t n, cudaStream_t st) {
+    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 64));
+    k_iota<<<grid > 0 ? grid : 1, 256, 0, st>>>(id, n);
+}
+
 void launch_foil(DevSpecies e, DevSpecies ion, int c0, int ncell, int ppc, uint64_t seed, cudaStream_t st) {
     const int64_t n = static_cast<int64_t>(ncell) * ppc;
     const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 64));

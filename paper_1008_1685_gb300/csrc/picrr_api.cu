@@ -556,6 +556,66 @@ pic_status pic_load_particles(pic_sim* s, int species, int64_t n, const int32_t*
     return PIC_OK;
 }
 
+pic_status pic_load_particles_f32(pic_sim* s, int species, int64_t n, const int32_t* cell, const float* off,
+                                  const float* px, const float* py, const float* pz, double weight, double charge,
+                                  double mass) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    if (species != PIC_ELECTRON && species != PIC_ION) return fail(s, PIC_ERR_INVALID_ARG, "bad species");
+    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "load_particles after the first step");
+    if (s->sp[species].loaded) return fail(s, PIC_ERR_STATE, "species already loaded");
+    if (n < 0 || n > 2147483647LL - 64) return fail(s, PIC_ERR_INVALID_ARG, "n must be in [0, 2^31 - 64]");
+    if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(s, PIC_ERR_INVALID_ARG, "NULL array");
+    if (!(mass > 0.0) || !std::isfinite(weight) || !std::isfinite(charge))
+        return fail(s, PIC_ERR_INVALID_ARG, "mass must be > 0, weight and charge finite");
+    bool sorted = true;
+    for (int64_t i = 0; i < n; ++i) {
+        if (cell[i] < 0 || cell[i] >= s->Nx) return fail(s, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
+        if (!(off[i] >= 0.0f && off[i] < 1.0f)) return fail(s, PIC_ERR_INVALID_ARG, "offset out of [0, 1)");
+        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]))
+            return fail(s, PIC_ERR_INVALID_ARG, "non-finite momentum");
+        if (i > 0 && cell[i] < cell[i - 1]) sorted = false;
+    }
+    if (!sorted) {
+        std::vector<double> o(off, off + n), x(px, px + n), y(py, py + n), z(pz, pz + n);
+        return pic_load_particles(s, species, n, cell, o.data(), x.data(), y.data(), z.data(), weight, charge,
+                                  mass);
+    }
+    DeviceGuard g(s->device);
+    std::vector<void*> fresh;
+    HostSpecies h;
+    pic_status st = alloc_species(s, h, n, fresh);
+    if (st != PIC_OK) {
+        release(s, fresh);
+        return st;
+    }
+    const DevSpecies& d = h.buf[0];
+    const size_t b4 = static_cast<size_t>(n) * 4;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(d.cell, cell, b4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.off, off, b4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.px, px, b4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.py, py, b4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.pz, pz, b4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) {
+            launch_iota(d.id, n, s->stream);
+            s->launches++;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        release(s, fresh);
+        return cuda_fail(s, e, "upload particles");
+    }
+    h.w = weight;
+    h.q = charge;
+    h.m = mass;
+    h.loaded = true;
+    s->sp[species] = h;
+    return PIC_OK;
+}
+
 pic_status pic_set_fields(pic_sim* s, const double* Ex, const double* Ey, const double* Ez, const double* By,
                           const double* Bz) {
     if (!s) return PIC_ERR_INVALID_ARG;

@@ -167,6 +167,7 @@ void launch_sort(const SortParams& S, int n_unit_blocks, cudaStream_t st, int* l
 void launch_build_units_from_sorted(const SortParams& S, cudaStream_t st, int* launches);
 
 void launch_foil(DevSpecies e, DevSpecies ion, int c0, int ncell, int ppc, uint64_t seed, cudaStream_t st);
+void launch_iota(int32_t* id, int64_t n, cudaStream_t st);
 
 // Diagnostics.
 struct DiagParams {
