@@ -141,6 +141,19 @@ def run_reference(args):
     return 0
 
 
+def aggregate(torch, dist, ms, particle_steps):
+    """Whole-job numbers across replicas: the slowest rank's time and the sum
+    of all ranks' particle steps (all_reduce MAX / SUM; identity at N = 1)."""
+    if dist is None or not dist.is_initialized():
+        return ms, particle_steps
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    n = torch.tensor([particle_steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def make_sim(picrr, device, w=LARGE):
     s = picrr.Sim(w["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], lambda_um=w["lambda_um"],
                   rr_on=w["rr_on"], sort_interval=w["sort_interval"], seed=w["seed"], device=device,
@@ -193,6 +206,8 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=40)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
+                    help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -214,7 +229,7 @@ def main():
     __graft_entry__.build()
     import paper_1008_1685_gb300 as picrr
 
-    w = LARGE
+    w = dict(LARGE, ppc=args.ppc)
     sim = make_sim(picrr, local)
     sim.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
     sim.inject_laser(w["a0"], w["pol"], 0, w["duration"])
@@ -242,13 +257,8 @@ def main():
     clk = clocks.stop() if clocks else None
     st1 = sim.stats()
     n_active_end = st1["active_particles"]
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    npart = torch.tensor([float(n_active) * args.steps], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(npart, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(npart.item()) / (ms_max / 1e3)
+    ms_max, total = aggregate(torch, dist, ms, float(n_active) * args.steps)
+    value = total / (ms_max / 1e3)
     push_avg_ms = st1["push_ms"] / max(1, st1["timed_push_launches"])
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_PARTICLE_STEP * n_active / (push_avg_ms / 1e3) / 1e9

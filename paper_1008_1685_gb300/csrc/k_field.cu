@@ -1,5 +1,6 @@
 // 1D Yee update of one step, with the current of this step, total-field /
-// scattered-field laser injection and first-order Mur ends:
+// scattered-field laser injection (incident values evaluated in double
+// precision by the host for each step) and first-order Mur ends:
 //   B^{n+1/2} = B^n - (dt/2) curl E^n,
 //   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J^{n+1/2}),
 //   B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1}.
@@ -8,44 +9,19 @@
 // (old and new fields live in separate buffers).  The block also converts
 // the fixed-point current to float, zeroes the accumulators of the next
 // step, adds the exact discrete Poynting flux through the two accounting
-// planes, and (block 0) sums the radiated energy of the push kernel's units
-// in a fixed order.
+// planes.
 #include "picrr_internal.cuh"
 
 namespace picrr {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-
-// Incident field at retarded time t (double precision phase and envelope):
-// Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az.
-__device__ void incident(const LaserParams& L, double t, float* ay, float* az) {
-    *ay = 0.f;
-    *az = 0.f;
-    if (!L.on || t < 0.0 || t > L.tau) return;
-    double g;
-    if (L.env == 0) {
-        const double q = sin(kPi * t / L.tau);
-        g = q * q;
-    } else if (t < L.rise) {
-        const double q = sin(0.5 * kPi * t / L.rise);
-        g = q * q;
-    } else if (t > L.tau - L.rise) {
-        const double q = sin(0.5 * kPi * (L.tau - t) / L.rise);
-        g = q * q;
-    } else {
-        g = 1.0;
-    }
-    double sn, cs;
-    sincos(t, &sn, &cs);
-    if (L.pol == 0) {
-        *ay = static_cast<float>(L.a0 * g * sn);
-    } else {
-        const double a = L.a0 * 0.70710678118654752440;
-        *ay = static_cast<float>(a * g * sn);
-        *az = static_cast<float>(-a * g * cs);
-    }
+// 64-bit fixed-point accumulator (2^fp units) to float from its two 32-bit
+// halves (32-bit conversions only): hi * 2^(32-fp) + lo * 2^-fp.
+__device__ __forceinline__ float fix_to_float(unsigned long long a, float lo_scale, float hi_scale) {
+    const int hi = static_cast<int>(static_cast<long long>(a) >> 32);
+    const unsigned lo = static_cast<unsigned>(a & 0xffffffffull);
+    return fmaf(static_cast<float>(hi), hi_scale, static_cast<float>(lo) * lo_scale);
 }
 
 __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
@@ -55,12 +31,10 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
     __shared__ float hBy[T + 3], hBz[T + 3];  // B^{n+1/2} on half nodes [i0-2, i0+T]
     __shared__ float nEy[T + 2], nEz[T + 2];  // E^{n+1} on nodes [i0-1, i0+T]
     __shared__ float sJy[T + 2], sJz[T + 2];  // J on nodes [i0-1, i0+T]
-    __shared__ double sred[32];
-
     const int tid = threadIdx.x;
     const int i0 = blockIdx.x * T;
     const int Nx = P.Nx, is = P.is;
-    const float c = P.c, hc = P.hc, fdt = P.fdt, fpi = P.fp_inv;
+    const float c = P.c, hc = P.hc, fdt = P.fdt, fpi = P.fp_inv, fph = P.fp_inv * 4294967296.0f;
 
     for (int q = tid; q < T + 4; q += T) {
         const int i = i0 - 2 + q + PADF;  // padded index, >= PADF - 2 >= 0
@@ -72,23 +46,20 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
             sBz[q] = in ? P.Fo[4][i] : 0.f;
         }
         if (q >= 1 && q < T + 3) {  // J on nodes [i0-1, i0+T]
-            sJy[q - 1] = in ? __ll2float_rn(static_cast<long long>(P.Jacc[1][i])) * fpi : 0.f;
-            sJz[q - 1] = in ? __ll2float_rn(static_cast<long long>(P.Jacc[2][i])) * fpi : 0.f;
+            sJy[q - 1] = in ? fix_to_float(P.Jacc[1][i], fpi, fph) : 0.f;
+            sJz[q - 1] = in ? fix_to_float(P.Jacc[2][i], fpi, fph) : 0.f;
         }
     }
     __syncthreads();
 
-    const double tn = static_cast<double>(P.n) * P.dt;
     // B^{n+1/2} on half nodes j = i0-2+q
     for (int q = tid; q < T + 3; q += T) {
         const int j = i0 - 2 + q;
         float by = sBy[q] + hc * (sEz[q + 1] - sEz[q]);
         float bz = sBz[q] - hc * (sEy[q + 1] - sEy[q]);
-        if (j == is - 1 && P.laser.on) {  // scattered side of the source plane: remove the incident E
-            float ay, az;
-            incident(P.laser, tn, &ay, &az);
-            bz += hc * ay;
-            by -= hc * az;
+        if (j == is - 1) {  // scattered side of the source plane: remove the incident E at t_n
+            bz += hc * P.inc[0];
+            by -= hc * P.inc[1];
         }
         hBy[q] = by;
         hBz[q] = bz;
@@ -101,11 +72,9 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         // node i: old E at sE[q+1], half nodes i-1, i at hB[q], hB[q+1]
         float ey = sEy[q + 1] - c * (hBz[q + 1] - hBz[q]) - fdt * sJy[q];
         float ez = sEz[q + 1] + c * (hBy[q + 1] - hBy[q]) - fdt * sJz[q];
-        if (i == is && P.laser.on) {  // total side: add the incident B at half node is-1/2
-            float ay, az;
-            incident(P.laser, tn + 0.5 * P.dt + 0.5 * P.dx, &ay, &az);
-            ey += c * ay;
-            ez += c * az;
+        if (i == is) {  // total side: add the incident B at half node is-1/2, time t_n + dt/2
+            ey += c * P.inc[2];
+            ez += c * P.inc[3];
         }
         if (i < 1 || i > Nx - 1) {
             ey = 0.f;
@@ -146,15 +115,13 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         if (i < Nx) {
             float by = hBy[q + 2] + hc * (nEz[q + 2] - nEz[q + 1]);
             float bz = hBz[q + 2] - hc * (nEy[q + 2] - nEy[q + 1]);
-            if (i == is - 1 && P.laser.on) {
-                float ay, az;
-                incident(P.laser, tn + P.dt, &ay, &az);
-                bz += hc * ay;
-                by -= hc * az;
+            if (i == is - 1) {  // incident E at t_{n+1}
+                bz += hc * P.inc[4];
+                by -= hc * P.inc[5];
             }
             P.Fn[3][pi] = by;
             P.Fn[4][pi] = bz;
-            const float jx = __ll2float_rn(static_cast<long long>(P.Jacc[0][pi])) * fpi;
+            const float jx = fix_to_float(P.Jacc[0][pi], fpi, fph);
             P.Jf[0][pi] = jx;
             P.Fn[0][pi] = P.Fo[0][pi] - fdt * jx;
         }
@@ -179,21 +146,6 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
             P.Jnext[0][pi] = 0ull;
             P.Jnext[1][pi] = 0ull;
             P.Jnext[2][pi] = 0ull;
-        }
-    }
-    // block 0: radiated energy of this step, fixed summation order
-    if (blockIdx.x == 0) {
-        const int nu = P.nunits[0];
-        double acc = 0.0;
-        for (int u = tid; u < nu; u += T) acc += P.rad_part[u];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((tid & 31) == 0) sred[tid >> 5] = acc;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < T / 32; ++w) t += sred[w];
-            P.tally[0] += t;
         }
     }
 }

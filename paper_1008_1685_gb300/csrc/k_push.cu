@@ -5,17 +5,23 @@
 // whose cells at the last sort lie in one tile).  Because cfl < 1 a particle
 // moves less than one cell per step, so k steps after the sort every
 // particle of the unit lies in [lo - k, hi + k]; the CTA stages the fields of
-// the window [lo - k - 1, hi + k + 2] into shared memory with one bulk TMA
-// copy per component and accumulates the unit's current there.
+// the window [lo - k - 1, hi + k + 2] and the unit's particle arrays (SoA)
+// into shared memory with bulk TMA copies completing on one mbarrier,
+// updates the particles in place, writes them back with bulk TMA stores and
+// accumulates the unit's current in shared memory.
 //
 // Determinism: each particle's current is split into at most two "bin"
 // records (its old cell and, if it crossed a boundary, its new cell), each
 // with five values (Jy and Jz shares of the bin's two nodes, and the Jx of
-// the bin's half node).  Warps sum runs of equal bins with a fixed-order
-// segmented shuffle reduction, convert the run sums to 64-bit fixed point
-// and add them with integer atomics, first into shared memory, then into the
-// global accumulators.  Integer addition is associative, so the result does
-// not depend on the order in which warps or CTAs arrive.
+// the bin's half node).  A thread first adds the old-bin records of its
+// successive particles that share a bin, in a fixed order; the
+// record is then converted to a 32-bit fixed-point value and the lanes of a
+// warp holding the same bin are summed exactly with an integer warp
+// reduction (match + reduce), whose total is shifted to the 64-bit scale of
+// the accumulators and added with one integer atomic per value, first into
+// shared memory, then into global memory.  Integer addition is exact and
+// associative, so the result does not depend on the order in which lanes,
+// warps or CTAs arrive.
 #include "picrr_internal.cuh"
 
 namespace picrr {
@@ -24,37 +30,25 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Sum runs of equal keys (in lane order) and add each run's total, scaled to
-// fixed point, to sJ[q][key].  key < 0 marks an empty record.
-__device__ __forceinline__ void seg_add(int key, float v0, float v1, float v2, float v3, float v4,
-                                        unsigned long long (*sJ)[WMAX], float scale) {
+// Add one bin record per lane to sJ[q][key]: lanes with equal keys are
+// summed exactly in 32-bit fixed point (2^lscale units, |value| < 2^26 per
+// lane), the sum is shifted to the accumulators' 2^fp units and added by the
+// group's first lane.  key < 0 marks an empty record.
+__device__ __forceinline__ void warp_add(int key, float v0, float v1, float v2, float v3, float v4,
+                                         unsigned long long (*sJ)[WMAX], float lscale, int shift) {
     const int lane = threadIdx.x & 31;
-    const int kprev = __shfl_up_sync(FULL, key, 1);
-    const bool head = (lane == 0) || (kprev != key);
-    const unsigned hm = __ballot_sync(FULL, head);
-    const int seg0 = 31 - __clz(hm & (FULL >> (31 - lane)));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const float t0 = __shfl_up_sync(FULL, v0, o);
-        const float t1 = __shfl_up_sync(FULL, v1, o);
-        const float t2 = __shfl_up_sync(FULL, v2, o);
-        const float t3 = __shfl_up_sync(FULL, v3, o);
-        const float t4 = __shfl_up_sync(FULL, v4, o);
-        if (lane - o >= seg0) {
-            v0 += t0;
-            v1 += t1;
-            v2 += t2;
-            v3 += t3;
-            v4 += t4;
-        }
-    }
-    const bool tail = ((hm >> 1) | 0x80000000u) >> lane & 1u;
-    if (tail && key >= 0) {
-        if (v0 != 0.f) atomicAdd(&sJ[0][key], static_cast<unsigned long long>(__float2ll_rn(v0 * scale)));
-        if (v1 != 0.f) atomicAdd(&sJ[1][key], static_cast<unsigned long long>(__float2ll_rn(v1 * scale)));
-        if (v2 != 0.f) atomicAdd(&sJ[2][key], static_cast<unsigned long long>(__float2ll_rn(v2 * scale)));
-        if (v3 != 0.f) atomicAdd(&sJ[3][key], static_cast<unsigned long long>(__float2ll_rn(v3 * scale)));
-        if (v4 != 0.f) atomicAdd(&sJ[4][key], static_cast<unsigned long long>(__float2ll_rn(v4 * scale)));
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int s0 = __reduce_add_sync(peers, __float2int_rn(v0 * lscale));
+    const int s1 = __reduce_add_sync(peers, __float2int_rn(v1 * lscale));
+    const int s2 = __reduce_add_sync(peers, __float2int_rn(v2 * lscale));
+    const int s3 = __reduce_add_sync(peers, __float2int_rn(v3 * lscale));
+    const int s4 = __reduce_add_sync(peers, __float2int_rn(v4 * lscale));
+    if (key >= 0 && lane == __ffs(peers) - 1) {
+        if (s0) atomicAdd(&sJ[0][key], static_cast<unsigned long long>(static_cast<long long>(s0) << shift));
+        if (s1) atomicAdd(&sJ[1][key], static_cast<unsigned long long>(static_cast<long long>(s1) << shift));
+        if (s2) atomicAdd(&sJ[2][key], static_cast<unsigned long long>(static_cast<long long>(s2) << shift));
+        if (s3) atomicAdd(&sJ[3][key], static_cast<unsigned long long>(static_cast<long long>(s3) << shift));
+        if (s4) atomicAdd(&sJ[4][key], static_cast<unsigned long long>(static_cast<long long>(s4) << shift));
     }
 }
 
@@ -63,7 +57,8 @@ __device__ __forceinline__ float comp(const float4& a, int j) {
     return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
 }
 
-__global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
+__global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) {
+    extern __shared__ __align__(128) unsigned char dsm[];  // particles of the unit: 5 x NPMAX words
     __shared__ __align__(128) float sF[5][WMAX];
     __shared__ __align__(16) unsigned long long sJ[NQ][WMAX];
     __shared__ __align__(8) uint64_t bar;
@@ -92,20 +87,36 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    const DevSpecies sp = P.sp[s];
+    // the unit's particles, from the aligned slot before `start` to the aligned
+    // slot after `end` (at most 3 particles of each neighbour, never written here)
+    const int base = start & ~3;
+    const int np4 = ((end + 3) & ~3) - base;  // <= UNIT_P + 6, a multiple of 4
+    int32_t* sC = reinterpret_cast<int32_t*>(dsm);
+    float* sO = reinterpret_cast<float*>(dsm) + NPMAX;
+    float* sX = sO + NPMAX;
+    float* sY = sX + NPMAX;
+    float* sZ = sY + NPMAX;
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
+        const uint32_t pb = static_cast<uint32_t>(np4) * 4u;
+        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u + 5u * pb);
+        tma_load_1d(sC, sp.cell + base, pb, &bar);
+        tma_load_1d(sO, sp.off + base, pb, &bar);
+        tma_load_1d(sX, sp.px + base, pb, &bar);
+        tma_load_1d(sY, sp.py + base, pb, &bar);
+        tma_load_1d(sZ, sp.pz + base, pb, &bar);
 #pragma unroll
         for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], P.F[c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
     }
 
-    const DevSpecies sp = P.sp[s];
     const float qm = P.qm[s], qw = P.qw[s];
-    const float cfl = P.cfl, dt = P.dt, eps = P.eps, scale = P.fp_scale;
+    const float cfl = P.cfl, dt = P.dt, eps = P.eps;
+    const float lscale = P.lscale[s];
+    const int shift = P.lshift[s];
     const bool rr = P.rr[s] != 0;
     const float hq = 0.5f * qm * dt;
     const float jxf = qw / cfl;  // q w dx / dt
-    const int base = start & ~3;
-    const int nslots = (end - base + 3) >> 2;
+    const int nslots = np4 >> 2;
     const int rounds = (nslots + PUSH_T - 1) / PUSH_T;
 
     const bool got = mbar_wait_bounded(&bar, 0);
@@ -118,6 +129,10 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
     }
 
     float rad = 0.f;
+    int rk = -1;  // running old-bin record of this thread
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f;
+    int rk2 = -1;  // running new-bin record
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;
     for (int r = 0; r < rounds; ++r) {
         const int slot = r * PUSH_T + tid;
         const int b4 = base + 4 * slot;
@@ -125,11 +140,11 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
         int4 c4 = make_int4(-1, -1, -1, -1);
         float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = o4, y4 = o4, z4 = o4;
         if (slot_ok) {
-            c4 = __ldcs(reinterpret_cast<const int4*>(sp.cell + b4));
-            o4 = __ldcs(reinterpret_cast<const float4*>(sp.off + b4));
-            x4 = __ldcs(reinterpret_cast<const float4*>(sp.px + b4));
-            y4 = __ldcs(reinterpret_cast<const float4*>(sp.py + b4));
-            z4 = __ldcs(reinterpret_cast<const float4*>(sp.pz + b4));
+            c4 = reinterpret_cast<const int4*>(sC)[slot];
+            o4 = reinterpret_cast<const float4*>(sO)[slot];
+            x4 = reinterpret_cast<const float4*>(sX)[slot];
+            y4 = reinterpret_cast<const float4*>(sY)[slot];
+            z4 = reinterpret_cast<const float4*>(sZ)[slot];
         }
         int cn[4];
         float fo[4], qx[4], qy[4], qz[4];
@@ -161,9 +176,9 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
                 const float b_z = (1.f - g) * sF[4][jb] + g * sF[4][jb + 1];
                 // --- Boris step for the Lorentz force (Bx = 0 in 1D)
                 const float mx = px + hq * e_x, my = py + hq * e_y, mz = pz + hq * e_z;
-                const float ig = 1.f / sqrtf(1.f + mx * mx + my * my + mz * mz);
+                const float ig = rsqrtf(1.f + mx * mx + my * my + mz * mz);
                 const float ty = hq * b_y * ig, tz = hq * b_z * ig;
-                const float sf = 2.f / (1.f + ty * ty + tz * tz);
+                const float sf = __fdividef(2.f, 1.f + ty * ty + tz * tz);
                 const float sy = sf * ty, sz = sf * tz;
                 const float ux = mx + my * tz - mz * ty;
                 const float uy = my - mx * tz;
@@ -174,7 +189,7 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
                 if (rr) {
                     // --- Eqs. (estim1, estimgamma): p(n) from p_L and p^{n-1/2}
                     const float bx_ = 0.5f * (lx + px), by_ = 0.5f * (ly + py), bz_ = 0.5f * (lz + pz);
-                    const float igb = 1.f / sqrtf(1.f + bx_ * bx_ + by_ * by_ + bz_ * bz_);
+                    const float igb = rsqrtf(1.f + bx_ * bx_ + by_ * by_ + bz_ * bz_);
                     const float vx = bx_ * igb, vy = by_ * igb, vz = bz_ * igb;
                     // f_L = -(E + v x B)
                     const float fx = -(e_x + vy * b_z - vz * b_y);
@@ -193,16 +208,17 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
                     py = ly + ky;
                     pz = lz + kz;
                     // gamma(p_L) - gamma(p^{n+1/2}) without cancellation
-                    const float gL = sqrtf(1.f + lx * lx + ly * ly + lz * lz);
-                    const float gN = sqrtf(1.f + px * px + py * py + pz * pz);
-                    rad -= (kx * (lx + px) + ky * (ly + py) + kz * (lz + pz)) / (gL + gN);
+                    const float qL = 1.f + lx * lx + ly * ly + lz * lz;
+                    const float qN = 1.f + px * px + py * py + pz * pz;
+                    const float gL = qL * rsqrtf(qL), gN = qN * rsqrtf(qN);
+                    rad -= __fdividef(kx * (lx + px) + ky * (ly + py) + kz * (lz + pz), gL + gN);
                 } else {
                     px = lx;
                     py = ly;
                     pz = lz;
                 }
                 // --- move: x^{n+1} = x^n + dt p_x / gamma, in cell units
-                const float ign = 1.f / sqrtf(1.f + px * px + py * py + pz * pz);
+                const float ign = rsqrtf(1.f + px * px + py * py + pz * pz);
                 const float vxn = px * ign, vyn = py * ign, vzn = pz * ign;
                 float fn = f + cfl * vxn;
                 int d = 0;
@@ -253,8 +269,40 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
                 c = store_c;
                 f = fn;
             }
-            seg_add(ko, vo0, vo1, vo2, vo3, vo4, sJ, scale);
-            if (__any_sync(FULL, kn >= 0)) seg_add(kn, vn0, vn1, vn2, vn3, vn4, sJ, scale);
+            // merge the old-bin record into this thread's running record
+            const bool merge = ko < 0 || rk < 0 || ko == rk;
+            if (__any_sync(FULL, !merge)) {
+                warp_add(merge ? -1 : rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
+                if (!merge) {
+                    rk = -1;
+                    r0 = r1 = r2 = r3 = r4 = 0.f;
+                }
+            }
+            if (ko >= 0) {
+                rk = ko;
+                r0 += vo0;
+                r1 += vo1;
+                r2 += vo2;
+                r3 += vo3;
+                r4 += vo4;
+            }
+            // new-bin records (boundary crossings) go to a second running record
+            const bool merge2 = kn < 0 || rk2 < 0 || kn == rk2;
+            if (__any_sync(FULL, !merge2)) {
+                warp_add(merge2 ? -1 : rk2, q0, q1, q2, q3, q4, sJ, lscale, shift);
+                if (!merge2) {
+                    rk2 = -1;
+                    q0 = q1 = q2 = q3 = q4 = 0.f;
+                }
+            }
+            if (kn >= 0) {
+                rk2 = kn;
+                q0 += vn0;
+                q1 += vn1;
+                q2 += vn2;
+                q3 += vn3;
+                q4 += vn4;
+            }
             act[j] = a;
             cn[j] = c;
             fo[j] = f;
@@ -262,37 +310,58 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
             qy[j] = py;
             qz[j] = pz;
         }
-        if (slot_ok) {
-            if (b4 >= start && b4 + 3 < end) {
-                __stcs(reinterpret_cast<int4*>(sp.cell + b4), make_int4(cn[0], cn[1], cn[2], cn[3]));
-                __stcs(reinterpret_cast<float4*>(sp.off + b4), make_float4(fo[0], fo[1], fo[2], fo[3]));
-                __stcs(reinterpret_cast<float4*>(sp.px + b4), make_float4(qx[0], qx[1], qx[2], qx[3]));
-                __stcs(reinterpret_cast<float4*>(sp.py + b4), make_float4(qy[0], qy[1], qy[2], qy[3]));
-                __stcs(reinterpret_cast<float4*>(sp.pz + b4), make_float4(qz[0], qz[1], qz[2], qz[3]));
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!act[j]) continue;
-                    sp.cell[b4 + j] = cn[j];
-                    sp.off[b4 + j] = fo[j];
-                    sp.px[b4 + j] = qx[j];
-                    sp.py[b4 + j] = qy[j];
-                    sp.pz[b4 + j] = qz[j];
-                }
-            }
+        if (slot_ok) {  // results back in place; the CTA writes them to global memory below
+            reinterpret_cast<int4*>(sC)[slot] = make_int4(cn[0], cn[1], cn[2], cn[3]);
+            reinterpret_cast<float4*>(sO)[slot] = make_float4(fo[0], fo[1], fo[2], fo[3]);
+            reinterpret_cast<float4*>(sX)[slot] = make_float4(qx[0], qx[1], qx[2], qx[3]);
+            reinterpret_cast<float4*>(sY)[slot] = make_float4(qy[0], qy[1], qy[2], qy[3]);
+            reinterpret_cast<float4*>(sZ)[slot] = make_float4(qz[0], qz[1], qz[2], qz[3]);
         }
     }
 
-    // radiated energy of the unit: fixed-order block reduction in double
-    double rd = static_cast<double>(rad);
+    // write the unit back: the 16-byte aligned interior with bulk TMA stores,
+    // the at most 3 + 3 particles at the ends (which share an aligned slot
+    // with a neighbouring unit) with plain stores
+    const int s4 = (start + 3) & ~3, e4 = end & ~3;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && e4 > s4) {
+        const uint32_t b = static_cast<uint32_t>(e4 - s4) * 4u, o = static_cast<uint32_t>(s4 - base);
+        tma_store_1d(sp.cell + s4, sC + o, b);
+        tma_store_1d(sp.off + s4, sO + o, b);
+        tma_store_1d(sp.px + s4, sX + o, b);
+        tma_store_1d(sp.py + s4, sY + o, b);
+        tma_store_1d(sp.pz + s4, sZ + o, b);
+        tma_store_commit();
+    }
+    if (tid < 8) {
+        const int h_end = min(s4, end), t_beg = max(e4, s4);
+        const int i = tid < 4 ? start + tid : t_beg + (tid - 4);
+        const bool ok = tid < 4 ? i < h_end : i < end;
+        if (ok) {
+            const int o = i - base;
+            sp.cell[i] = sC[o];
+            sp.off[i] = sO[o];
+            sp.px[i] = sX[o];
+            sp.py[i] = sY[o];
+            sp.pz[i] = sZ[o];
+        }
+    }
+
+    // a thread holds at most 12 particles of a unit (UNIT_P / PUSH_T + 4), so a
+    // running record stays below 16 particles: |record| < 2^26 / 32 per lane
+    warp_add(rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
+    if (__any_sync(FULL, rk2 >= 0)) warp_add(rk2, q0, q1, q2, q3, q4, sJ, lscale, shift);
+
+    // radiated energy of the unit: fixed-order warp reduction, warps summed in double
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rd += __shfl_xor_sync(FULL, rd, o);
-    if (lane == 0) sred[warp] = rd;
+    for (int o = 16; o > 0; o >>= 1) rad += __shfl_xor_sync(FULL, rad, o);
+    if (lane == 0) sred[warp] = static_cast<double>(rad);
     __syncthreads();  // also orders every shared-memory current update before the flush
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < PUSH_T / 32; ++w) t += sred[w];
-        P.rad_part[u] = t * static_cast<double>(P.rad_w[s]);
+        P.rad_part[u] += t * static_cast<double>(P.rad_w[s]);  // summed into the tally at the next flush
     }
     // flush the window: node n gets jy_lo of bin n and jy_hi of bin n-1
     for (int i = tid; i < L; i += PUSH_T) {
@@ -303,13 +372,20 @@ __global__ void __launch_bounds__(PUSH_T) k_push_deposit(const PushParams P) {
         if (jy) atomicAdd(P.J[1] + p0 + i, jy);
         if (jz) atomicAdd(P.J[2] + p0 + i, jz);
     }
+    if (tid == 0) tma_store_wait_read();  // shared memory must outlive the bulk stores' reads
 }
 
 }  // namespace
 
 void launch_push(const PushParams& P, int grid, cudaStream_t st) {
     if (grid <= 0) return;
-    k_push_deposit<<<grid, PUSH_T, 0, st>>>(P);
+    constexpr size_t dyn = 5u * NPMAX * 4u;
+    static bool attr = false;  // per process; the attribute is per function and device-independent
+    if (!attr) {
+        cudaFuncSetAttribute(k_push_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
+        attr = true;
+    }
+    k_push_deposit<<<grid, PUSH_T, dyn, st>>>(P);
 }
 
 }  // namespace picrr

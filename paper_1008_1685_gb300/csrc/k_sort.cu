@@ -28,6 +28,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SORT_T = 256;
 constexpr int SCAN_T = 1024;
+constexpr int KEY_T = 256;  // keys per block of the per-cell kernels
 constexpr int ESC = SSTR - 1;  // local slot of particles frozen since the last sort
 
 __device__ __forceinline__ int unit_base(const UnitTable& U, int s) { return s == 0 ? 0 : U.count[1]; }
@@ -44,15 +45,25 @@ __global__ void __launch_bounds__(SORT_T) k_sort_count(const SortParams S) {
     for (int i = threadIdx.x; i < SSTR; i += SORT_T) cnt[i] = 0;
     __syncthreads();
     const int32_t* cell = S.src[s].cell;
-    for (int i = start + threadIdx.x; i < end; i += SORT_T) {
-        const int c = cell[i];
-        if (c < 0) {
-            atomicAdd(&cnt[ESC], 1);
-        } else {
-            const int l = c - wb;
-            if (l >= 0 && l < L && l < ESC) atomicAdd(&cnt[l], 1);
-            else atomicOr(S.meta + 4, ST_WINDOW);
+    const int lane = threadIdx.x & 31;
+    for (int i0 = start; i0 < end; i0 += SORT_T) {  // block-uniform trip count
+        const int i = i0 + threadIdx.x;
+        int l = -1;
+        if (i < end) {
+            const int c = cell[i];
+            if (c < 0) {
+                l = ESC;
+            } else {
+                l = c - wb;
+                if (!(l >= 0 && l < L && l < ESC)) {
+                    atomicOr(S.meta + 4, ST_WINDOW);
+                    l = -1;
+                }
+            }
         }
+        // lanes with the same cell add their count once
+        const unsigned peers = __match_any_sync(FULL, l);
+        if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[l], __popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < SSTR; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = (i == ESC) ? 0 : cnt[i];
@@ -79,106 +90,151 @@ __device__ void covering(const SortParams& S, int s, int key, int& u0, int& u1) 
     u1 = b + l - 1;
 }
 
-// ---- 2a. per-cell totals ----------------------------------------------------
-__global__ void k_sort_totals(const SortParams S) {
-    const int s = blockIdx.y;
-    const int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= S.Nx) return;
-    int u0, u1;
-    covering(S, s, key, u0, u1);
-    int tot = 0;
-    for (int u = u0; u <= u1; ++u) {
-        const int l = key - (S.units.lo[u] - S.k);
-        if (l >= 0 && l < ESC) tot += S.cnt[static_cast<size_t>(u) * SSTR + l];
-    }
-    S.keycount[s][key] = tot;
+__device__ __forceinline__ int block_sum_int(int v, int* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    int t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < KEY_T / 32; ++w) t += sh[w];
+    return t;
 }
 
-// ---- 2b. exclusive scan of the cell totals (one block per species) --------
-// keystart[s][0..Nx], keystart[Nx] = active count.  Also the escape offsets
-// of the units (after the active particles) and meta[2+s] = new escapes.
-__global__ void __launch_bounds__(SCAN_T) k_sort_scan(const SortParams S, int with_units) {
-    __shared__ int warp_tot[SCAN_T / 32];
-    __shared__ int carry;
-    const int s = blockIdx.x;
+// exclusive scan of v over the block (KEY_T threads), plus the block total
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < KEY_T / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < KEY_T / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    const int r = x - v + (warp > 0 ? sh[warp - 1] : 0);
+    *total = sh[KEY_T / 32 - 1];
+    return r;
+}
+
+// ---- 2a. per-cell totals (and per-block sums of them) -------------------------
+__global__ void __launch_bounds__(KEY_T) k_sort_totals(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
+    const int s = blockIdx.y;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    int tot = 0;
+    if (key < S.Nx) {
+        int u0, u1;
+        covering(S, s, key, u0, u1);
+        for (int u = u0; u <= u1; ++u) {
+            const int l = key - (S.units.lo[u] - S.k);
+            if (l >= 0 && l < ESC) tot += S.cnt[static_cast<size_t>(u) * SSTR + l];
+        }
+        S.keycount[s][key] = tot;
+    }
+    const int b = block_sum_int(tot, sh);
+    if (threadIdx.x == 0) S.blocksum[s][blockIdx.x] = b;
+}
+
+// per-block sums of key counts filled by atomics (fresh load)
+__global__ void __launch_bounds__(KEY_T) k_block_sums(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
+    const int s = blockIdx.y;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    const int v = key < S.Nx ? S.keycount[s][key] : 0;
+    const int b = block_sum_int(v, sh);
+    if (threadIdx.x == 0) S.blocksum[s][blockIdx.x] = b;
+}
+
+// exclusive scan of n ints held contiguously, by one block of SCAN_T threads
+// (each thread a contiguous range); writes out[0..n) and returns the total
+__device__ int block_scan_ranges(const int32_t* in, int32_t* out, int n, int* sh) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = S.Nx;
     const int per = (n + SCAN_T - 1) / SCAN_T;
     const int a = min(n, tid * per), b = min(n, a + per);
     int sum = 0;
-    for (int i = a; i < b; ++i) sum += S.keycount[s][i];
-    // block exclusive scan of the per-thread sums
+    for (int i = a; i < b; ++i) sum += in[i];
     int x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(FULL, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (lane == 31) sh[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int w = warp_tot[lane];
+        int w = sh[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, w, o);
             if (lane >= o) w += y;
         }
-        warp_tot[lane] = w;  // inclusive over warps
+        sh[lane] = w;
     }
     __syncthreads();
-    int run = x - sum + (warp > 0 ? warp_tot[warp - 1] : 0);
+    int run = x - sum + (warp > 0 ? sh[warp - 1] : 0);
     for (int i = a; i < b; ++i) {
-        S.keystart[s][i] = run;
-        run += S.keycount[s][i];
+        const int v = in[i];
+        out[i] = run;
+        run += v;
     }
-    if (tid == SCAN_T - 1) {
-        S.keystart[s][n] = warp_tot[SCAN_T / 32 - 1];
-        carry = warp_tot[SCAN_T / 32 - 1];
-    }
-    if (!with_units) return;
+    const int total = sh[SCAN_T / 32 - 1];
     __syncthreads();
-    // escape offsets of the units of species s, in unit order
-    const int ub = unit_base(S.units, s), nu = S.units.count[1 + s];
-    const int act = carry;
-    __syncthreads();
-    int base = 0;
-    for (int c0 = 0; c0 < nu; c0 += SCAN_T) {
-        const int u = c0 + tid;
-        const int v = (u < nu) ? S.esc_cnt[ub + u] : 0;
-        int y = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int z = __shfl_up_sync(FULL, y, o);
-            if (lane >= o) y += z;
-        }
-        __syncthreads();
-        if (lane == 31) warp_tot[warp] = y;
-        __syncthreads();
-        if (warp == 0) {
-            int w = warp_tot[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int z = __shfl_up_sync(FULL, w, o);
-                if (lane >= o) w += z;
-            }
-            warp_tot[lane] = w;
-        }
-        __syncthreads();
-        const int excl = base + y - v + (warp > 0 ? warp_tot[warp - 1] : 0);
-        if (u < nu) S.esc_off[ub + u] = act + excl;
-        base += warp_tot[SCAN_T / 32 - 1];
-    }
-    if (tid == 0) S.meta[2 + s] = base;
+    return total;
 }
 
-// ---- 2c. destination of every (unit, cell) pair ---------------------------
-__global__ void k_sort_offsets(const SortParams S) {
+// ---- 2b. scan of the per-block key sums; escape offsets of the units ----------
+// One block per species.  blockstart[s][b] = keys before block b; keystart[s][Nx]
+// = active particles; esc_off[u] = destination of unit u's first escaped
+// particle (after all active ones); meta[2+s] = escapes since the last sort.
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const SortParams S, int nkb, int with_units) {
+    __shared__ int sh[SCAN_T / 32];
+    const int s = blockIdx.x;
+    const int act = block_scan_ranges(S.blocksum[s], S.blockstart[s], nkb, sh);
+    if (threadIdx.x == 0) S.keystart[s][S.Nx] = act;
+    if (!with_units) return;
+    const int ub = unit_base(S.units, s), nu = S.units.count[1 + s];
+    const int esc = block_scan_ranges(S.esc_cnt + ub, S.esc_off + ub, nu, sh);
+    for (int u = threadIdx.x; u < nu; u += SCAN_T) S.esc_off[ub + u] += act;
+    if (threadIdx.x == 0) S.meta[2 + s] = esc;
+}
+
+// keystart[s][key] from the block starts and a block scan of the key counts
+__global__ void __launch_bounds__(KEY_T) k_keystart(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
     const int s = blockIdx.y;
-    const int key = blockIdx.x * blockDim.x + threadIdx.x;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    const int v = key < S.Nx ? S.keycount[s][key] : 0;
+    int total;
+    const int r = block_excl_scan(v, sh, &total);
+    if (key < S.Nx) S.keystart[s][key] = S.blockstart[s][blockIdx.x] + r;
+}
+
+// ---- 2c. cell starts and the destination of every (unit, cell) pair ----------
+__global__ void __launch_bounds__(KEY_T) k_sort_offsets(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
+    const int s = blockIdx.y;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    const int v = key < S.Nx ? S.keycount[s][key] : 0;
+    int total;
+    const int r = block_excl_scan(v, sh, &total);
     if (key >= S.Nx) return;
+    int run = S.blockstart[s][blockIdx.x] + r;
+    S.keystart[s][key] = run;
     int u0, u1;
     covering(S, s, key, u0, u1);
-    int run = S.keystart[s][key];
     for (int u = u0; u <= u1; ++u) {
         const int l = key - (S.units.lo[u] - S.k);
         if (l >= 0 && l < ESC) {
@@ -258,97 +314,98 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
     }
 }
 
-// ---- 4. unit table from sorted cells (one block, both species) -------------
-__global__ void __launch_bounds__(SCAN_T) k_build_units(const SortParams S) {
-    __shared__ int warp_tot[SCAN_T / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// ---- 4. unit table from sorted cells ------------------------------------------
+// 4a. units per tile (TILE cells, at most UNIT_P particles a unit), scanned
+// per species by one block: tile_first[s][t] = first unit of tile t.
+__global__ void __launch_bounds__(SCAN_T) k_tile_units(const SortParams S) {
+    __shared__ int sh[SCAN_T / 32];
     const int ntiles = (S.Nx + TILE - 1) / TILE;
-    int ubase = 0;
+    int base = 0;
     for (int s = 0; s < 2; ++s) {
         const int32_t* ks = S.keystart[s];
-        const int32_t* cell = S.dst[s].cell;
-        int run = 0;
-        for (int t0 = 0; t0 < ntiles; t0 += SCAN_T) {
-            const int t = t0 + tid;
-            int nt = 0, ts = 0, te = 0;
-            if (t < ntiles) {
-                ts = ks[t * TILE];
-                te = ks[min((t + 1) * TILE, S.Nx)];
-                nt = (te - ts + UNIT_P - 1) / UNIT_P;
-            }
-            int y = nt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int z = __shfl_up_sync(FULL, y, o);
-                if (lane >= o) y += z;
-            }
-            __syncthreads();
-            if (lane == 31) warp_tot[warp] = y;
-            __syncthreads();
-            if (warp == 0) {
-                int w = warp_tot[lane];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int z = __shfl_up_sync(FULL, w, o);
-                    if (lane >= o) w += z;
-                }
-                warp_tot[lane] = w;
-            }
-            __syncthreads();
-            const int first = ubase + run + y - nt + (warp > 0 ? warp_tot[warp - 1] : 0);
-            for (int r = 0; r < nt; ++r) {
-                const int u = first + r;
-                if (u >= S.max_units) break;  // cannot happen: max_units bounds the count
-                const int a = ts + r * UNIT_P, b = min(a + UNIT_P, te);
-                S.units.species[u] = s;
-                S.units.start[u] = a;
-                S.units.end[u] = b;
-                S.units.lo[u] = cell[a];
-                S.units.hi[u] = cell[b - 1];
-            }
-            run += warp_tot[SCAN_T / 32 - 1];
+        for (int t = threadIdx.x; t < ntiles; t += SCAN_T) {
+            const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, S.Nx)];
+            S.tile_n[s][t] = (te - ts + UNIT_P - 1) / UNIT_P;
         }
-        if (tid == 0) {
-            S.units.count[1 + s] = run;
+        __syncthreads();
+        const int nu = block_scan_ranges(S.tile_n[s], S.tile_first[s], ntiles, sh);
+        if (threadIdx.x == 0) {
+            S.tile_first[s][ntiles] = nu;
+            S.units.count[1 + s] = nu;
             S.meta[s] = ks[S.Nx];  // active particles at this sort
         }
-        ubase += run;
+        base += nu;
         __syncthreads();
     }
-    if (tid == 0) S.units.count[0] = min(ubase, S.max_units);
+    if (threadIdx.x == 0) S.units.count[0] = min(base, S.max_units);
+}
+
+// 4b. one thread per unit
+__global__ void k_fill_units(const SortParams S) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= S.units.count[0]) return;
+    const int n0 = S.units.count[1];
+    const int s = u < n0 ? 0 : 1;
+    const int v = u - (s ? n0 : 0);
+    const int ntiles = (S.Nx + TILE - 1) / TILE;
+    const int32_t* tf = S.tile_first[s];
+    int l = 0, r = ntiles;  // last tile t with tf[t] <= v
+    while (r - l > 1) {
+        const int m = (l + r) >> 1;
+        if (tf[m] <= v) l = m; else r = m;
+    }
+    const int t = l;
+    const int32_t* ks = S.keystart[s];
+    const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, S.Nx)];
+    const int a = ts + (v - tf[t]) * UNIT_P;
+    const int b = min(a + UNIT_P, te);
+    S.units.species[u] = s;
+    S.units.start[u] = a;
+    S.units.end[u] = b;
+    S.units.lo[u] = S.dst[s].cell[a];
+    S.units.hi[u] = S.dst[s].cell[b - 1];
 }
 
 // ---- histogram of sorted, freshly loaded particles ---------------------------
+// warp-aggregated: lanes holding the same cell add their count once
 __global__ void k_hist(const SortParams S) {
     const int s = blockIdx.y;
     const int64_t n = S.n[s];
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int c = S.dst[s].cell[i];
-        if (c >= 0 && c < S.Nx) atomicAdd(&S.keycount[s][c], 1);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); b < n;
+         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = b + lane;
+        const int c = i < n ? S.dst[s].cell[i] : -1;
+        const unsigned peers = __match_any_sync(FULL, c);
+        if (c >= 0 && c < S.Nx && lane == __ffs(peers) - 1) atomicAdd(&S.keycount[s][c], __popc(peers));
     }
 }
 
 }  // namespace
 
 void launch_sort(const SortParams& S, int n_unit_blocks, cudaStream_t st, int* launches) {
-    const int kb = (S.Nx + 255) / 256;
+    const int kb = (S.Nx + KEY_T - 1) / KEY_T;
     k_sort_count<<<n_unit_blocks, SORT_T, 0, st>>>(S);
-    k_sort_totals<<<dim3(kb, 2), 256, 0, st>>>(S);
-    k_sort_scan<<<2, SCAN_T, 0, st>>>(S, 1);
-    k_sort_offsets<<<dim3(kb, 2), 256, 0, st>>>(S);
+    k_sort_totals<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
+    k_scan_blocks<<<2, SCAN_T, 0, st>>>(S, kb, 1);
+    k_sort_offsets<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
     k_sort_scatter<<<n_unit_blocks + 64, SORT_T, 0, st>>>(S);
-    k_build_units<<<1, SCAN_T, 0, st>>>(S);
-    *launches += 6;
+    k_tile_units<<<1, SCAN_T, 0, st>>>(S);
+    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S);
+    *launches += 7;
 }
 
 void launch_build_units_from_sorted(const SortParams& S, cudaStream_t st, int* launches) {
+    const int kb = (S.Nx + KEY_T - 1) / KEY_T;
     cudaMemsetAsync(S.keycount[0], 0, sizeof(int32_t) * (S.Nx + 2), st);
     cudaMemsetAsync(S.keycount[1], 0, sizeof(int32_t) * (S.Nx + 2), st);
     k_hist<<<dim3(256, 2), 256, 0, st>>>(S);
-    k_sort_scan<<<2, SCAN_T, 0, st>>>(S, 0);
-    k_build_units<<<1, SCAN_T, 0, st>>>(S);
-    *launches += 3;
+    k_block_sums<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
+    k_scan_blocks<<<2, SCAN_T, 0, st>>>(S, kb, 0);
+    k_keystart<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
+    k_tile_units<<<1, SCAN_T, 0, st>>>(S);
+    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S);
+    *launches += 6;
 }
 
 // ---- foil loader -------------------------------------------------------------

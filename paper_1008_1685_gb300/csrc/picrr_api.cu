@@ -67,6 +67,7 @@ struct pic_sim {
     double* rad_part = nullptr;
     int32_t *cnt = nullptr, *offs = nullptr, *esc_cnt = nullptr, *esc_off = nullptr;
     int32_t *keycount[2] = {}, *keystart[2] = {}, *meta = nullptr;
+    int32_t *blocksum[2] = {}, *blockstart[2] = {}, *tile_n[2] = {}, *tile_first[2] = {};
 
     int64_t step = 0;
     int since_sort = 0;
@@ -243,6 +244,10 @@ SortParams sort_params(pic_sim* s) {
         S.n[k] = s->sp[k].loaded ? s->sp[k].n : 0;
         S.keycount[k] = s->keycount[k];
         S.keystart[k] = s->keystart[k];
+        S.blocksum[k] = s->blocksum[k];
+        S.blockstart[k] = s->blockstart[k];
+        S.tile_n[k] = s->tile_n[k];
+        S.tile_first[k] = s->tile_first[k];
     }
     S.units = s->units;
     S.cnt = s->cnt;
@@ -291,6 +296,11 @@ pic_status prepare(pic_sim* s) {
     for (int k = 0; k < 2; ++k) {
         if ((st = dalloc_t(s, &s->keycount[k], static_cast<size_t>(s->Nx) + 2, &fresh)) != PIC_OK) goto bad;
         if ((st = dalloc_t(s, &s->keystart[k], static_cast<size_t>(s->Nx) + 2, &fresh)) != PIC_OK) goto bad;
+        const size_t nkb = static_cast<size_t>(s->Nx) / 256 + 2, ntl = static_cast<size_t>(s->Nx) / TILE + 3;
+        if ((st = dalloc_t(s, &s->blocksum[k], nkb, &fresh)) != PIC_OK) goto bad;
+        if ((st = dalloc_t(s, &s->blockstart[k], nkb, &fresh)) != PIC_OK) goto bad;
+        if ((st = dalloc_t(s, &s->tile_n[k], ntl, &fresh)) != PIC_OK) goto bad;
+        if ((st = dalloc_t(s, &s->tile_first[k], ntl, &fresh)) != PIC_OK) goto bad;
     }
     if ((st = dalloc_t(s, &s->meta, 8, &fresh)) != PIC_OK) goto bad;
     {
@@ -315,6 +325,7 @@ bad:
     s->rad_part = nullptr;
     s->cnt = s->offs = s->esc_cnt = s->esc_off = s->meta = nullptr;
     s->keycount[0] = s->keycount[1] = s->keystart[0] = s->keystart[1] = nullptr;
+    for (int k = 0; k < 2; ++k) s->blocksum[k] = s->blockstart[k] = s->tile_n[k] = s->tile_first[k] = nullptr;
     return st;
 }
 
@@ -338,8 +349,48 @@ PushParams push_params(pic_sim* s) {
     P.cfl = static_cast<float>(s->cfl);
     P.dt = static_cast<float>(s->dt);
     P.eps = static_cast<float>(s->eps);
-    P.fp_scale = std::ldexp(1.0f, s->fp_bits);
+    for (int k = 0; k < 2; ++k) {
+        // a warp record sums at most 16 particles of one lane (a thread holds at
+        // most UNIT_P / PUSH_T + 4 particles of a unit) over 32 lanes, each value
+        // bounded by |q w| max(1, 1/cfl): keep every lane below 2^26
+        static_assert(UNIT_P / PUSH_T + 4 <= 16, "running record bound");
+        const double vmax = std::fabs(s->sp[k].q * s->sp[k].w) * std::max(1.0, 1.0 / s->cfl);
+        int ls = 40;
+        if (vmax > 0.0) ls = static_cast<int>(std::floor(26.0 - std::log2(16.0 * vmax)));
+        ls = std::min(ls, s->fp_bits);
+        P.lscale[k] = std::ldexp(1.0f, ls);
+        P.lshift[k] = s->fp_bits - ls;
+    }
     return P;
+}
+
+// Incident field of the laser at retarded time t (double precision phase and
+// envelope): Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az.  LP: ay = a0 g sin t;
+// CP: a0/sqrt2 per component, ay = a g sin t, az = -a g cos t.
+void incident(const LaserParams& L, double t, float* ay, float* az) {
+    *ay = 0.f;
+    *az = 0.f;
+    if (!L.on || t < 0.0 || t > L.tau) return;
+    double g;
+    if (L.env == PIC_ENV_SIN2) {
+        const double q = std::sin(kPi * t / L.tau);
+        g = q * q;
+    } else if (t < L.rise) {
+        const double q = std::sin(0.5 * kPi * t / L.rise);
+        g = q * q;
+    } else if (t > L.tau - L.rise) {
+        const double q = std::sin(0.5 * kPi * (L.tau - t) / L.rise);
+        g = q * q;
+    } else {
+        g = 1.0;
+    }
+    if (L.pol == PIC_LP) {
+        *ay = static_cast<float>(L.a0 * g * std::sin(t));
+    } else {
+        const double a = L.a0 / std::sqrt(2.0);
+        *ay = static_cast<float>(a * g * std::sin(t));
+        *az = static_cast<float>(-a * g * std::cos(t));
+    }
 }
 
 FieldParams field_params(pic_sim* s) {
@@ -354,8 +405,6 @@ FieldParams field_params(pic_sim* s) {
         Q.Jf[c] = s->Jf[c];
     }
     Q.tally = s->tally;
-    Q.rad_part = s->rad_part;
-    Q.nunits = s->units.count;
     Q.Nx = s->Nx;
     Q.is = s->is;
     Q.glen = static_cast<int>(s->glen);
@@ -366,7 +415,9 @@ FieldParams field_params(pic_sim* s) {
     Q.hc = static_cast<float>(0.5 * s->cfl);
     Q.fdt = static_cast<float>(s->dt);
     Q.fp_inv = std::ldexp(1.0f, -s->fp_bits);
-    Q.laser = s->laser;
+    const double tn = static_cast<double>(s->step) * s->dt;
+    const double ts[3] = {tn, tn + 0.5 * s->dt + 0.5 * s->dx, tn + s->dt};
+    for (int k = 0; k < 3; ++k) incident(s->laser, ts[k], &Q.inc[2 * k], &Q.inc[2 * k + 1]);
     return Q;
 }
 
@@ -661,11 +712,18 @@ pic_status pic_inject_laser(pic_sim* s, double a0, int polarization, int envelop
     return PIC_OK;
 }
 
+// Add the per-unit radiated energy into the tally (before the units change).
+static void rad_flush(pic_sim* s) {
+    launch_rad_flush(s->rad_part, s->units.count, s->tally, s->stream);
+    s->launches++;
+}
+
 static pic_status do_sort(pic_sim* s) {
     SortParams S = sort_params(s);
     int nl = 0;
     {
         Timed t(s, 2);
+        rad_flush(s);
         launch_sort(S, s->max_units, s->stream, &nl);
     }
     s->launches += nl;
@@ -705,6 +763,7 @@ pic_status pic_step_n(pic_sim* s, int64_t n, int64_t* steps_done) {
             if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
         }
     }
+    if (n > 0 && s->since_sort > 0) rad_flush(s);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "step");

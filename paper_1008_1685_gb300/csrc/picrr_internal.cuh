@@ -24,6 +24,7 @@ constexpr int TILE = 64;          // cells per tile: bounds the cell span of a u
 constexpr int UNIT_P = 2048;      // particles per unit at most
 constexpr int KMAX = 32;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
+constexpr int NPMAX = UNIT_P + 8;  // particle slots of a unit staged in shared memory (multiple of 4)
 constexpr int WMAX = 144;         // window length bound in the push kernel (>= TILE + 2 KMAX + 10)
 constexpr int SSTR = TILE + 2 * KMAX + 4;  // per-unit key-window stride of the sort scratch
 constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
@@ -61,12 +62,13 @@ struct PushParams {
     const float* F[5];  // Ex, Ey, Ez, By, Bz, each pointing at element 0 of the padded array
     unsigned long long* J[3];  // Jx, Jy, Jz accumulators (padded)
     UnitTable units;
-    double* rad_part;   // [max_units] radiated energy of each unit this step
+    double* rad_part;   // [max_units] radiated energy of each unit since the last flush
     int* status;
     int Nx;
     int k;              // steps since the last sort
     float cfl, dt, eps;
-    float fp_scale;     // 2^fp
+    float lscale[2];    // per-species 32-bit fixed-point scale of a warp record (power of two)
+    int lshift[2];      // fp - log2(lscale): shift from warp records to accumulator units
 };
 
 struct LaserParams {
@@ -81,15 +83,15 @@ struct FieldParams {
     unsigned long long* Jnext[3];       // zeroed for the next step
     float* Jf[3];        // float J of this step (read-back)
     double* tally;       // [0] radiated, [1] flux in, [2] flux out
-    const double* rad_part;
-    const int32_t* nunits;
     int Nx, is;
     int glen;            // length of every padded grid array
     int64_t n;           // step index (t_n = n dt)
     double dt, dx;
     float c, hc, fdt;    // cfl, cfl/2, dt
     float fp_inv;        // 2^-fp
-    LaserParams laser;
+    // incident field (ay, az) at retarded times t_n (source node), t_n + dt/2 + dx/2
+    // (half node before it) and t_{n+1}: Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az
+    float inc[6];
 };
 
 // ---------------------------------------------------------------------------
@@ -141,6 +143,19 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
         : "memory");
 }
 
+// 1D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from this CTA's shared memory to global memory, in the current bulk group.
+__device__ __forceinline__ void tma_store_1d(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void tma_store_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (each defined in its own translation unit).
 // ---------------------------------------------------------------------------
@@ -159,6 +174,10 @@ struct SortParams {
     int32_t* keystart[2];  // [Nx + 2]; keystart[Nx] = active count
     int32_t* meta;         // [8]: [0..1] active particles at the last sort, [2..3] escapes since,
                            // [4] error bits of the sort
+    int32_t* blocksum[2];  // [Nx/256 + 1] key counts per block of 256 cells
+    int32_t* blockstart[2];
+    int32_t* tile_n[2];    // [Nx/TILE + 1] units per tile
+    int32_t* tile_first[2];  // [Nx/TILE + 2] first unit of each tile
     int Nx, k, max_units;
 };
 // Full re-sort of both species (bounded displacement since the last sort).
@@ -179,6 +198,8 @@ struct DiagParams {
 int launch_field_energy(const DiagParams& D, double* partials, int max_blocks, cudaStream_t st);
 int launch_kinetic(DevSpecies sp, int64_t n, double* partials, int max_blocks, cudaStream_t st);
 void launch_reduce_partials(const double* partials, int n, double scale, double* out, cudaStream_t st);
+// tally[0] += sum of rad_part[0 .. units.count[0]) in a fixed order; zero them.
+void launch_rad_flush(double* rad_part, const int32_t* unit_count, double* tally, cudaStream_t st);
 void launch_spectrum(DevSpecies sp, int64_t n, double mass_mev, int nbins, double e_min, double e_max,
                      unsigned long long* bins, cudaStream_t st);
 

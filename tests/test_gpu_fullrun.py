@@ -1,0 +1,228 @@
+"""GPU parity on whole runs and at full benchmark size.
+
+- small single run (20 lambda, lambda/200, 12,800 + 12,800 particles, LP a0 = 200,
+  4211 steps = 20 periods): energy bookkeeping within 1e-3 of the injected
+  energy; ion spectra of 16-seed ensembles: mean energy within 2 %, peak and
+  FWHM within the oracle's own ensemble-to-ensemble spread;
+- paper-scale grid (60,000 cells, 400 + 400 particles per cell) over its first
+  500 steps, with the foil and a short pulse placed so that the pulse peak
+  reaches the foil inside the window;
+- the large benchmark run (200,000 cells, 32M + 32M particles) in the launch
+  configuration bench.py times: sampled particles recomputed one by one by
+  the oracle from the GPU's own fields, plus Gauss's law over the whole grid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2 * math.pi
+
+
+@pytest.fixture(scope="module")
+def picrr():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1008_1685_gb300 as m
+
+    return m
+
+
+def peak_fwhm(counts, e_min, e_max, sigma_bins=6.0):
+    """Peak energy and FWHM of a binned spectrum after Gaussian smoothing
+    (sigma in bins); parabolic peak interpolation, linear interpolation of the
+    half-maximum crossings on each side of the peak."""
+    nb = len(counts)
+    w = (e_max - e_min) / nb
+    x = np.arange(-int(4 * sigma_bins), int(4 * sigma_bins) + 1)
+    k = np.exp(-0.5 * (x / sigma_bins) ** 2)
+    s = np.convolve(counts, k / k.sum(), mode="same")
+    i = int(np.argmax(s))
+    d = 0.0
+    if 0 < i < nb - 1:
+        a, b, c = s[i - 1], s[i], s[i + 1]
+        den = a - 2 * b + c
+        d = 0.5 * (a - c) / den if den != 0 else 0.0
+    peak = e_min + (i + 0.5 + d) * w
+    half = 0.5 * s[i]
+    lo = i
+    while lo > 0 and s[lo] > half:
+        lo -= 1
+    hi = i
+    while hi < nb - 1 and s[hi] > half:
+        hi += 1
+    x_lo = lo + (half - s[lo]) / (s[lo + 1] - s[lo]) if s[lo + 1] != s[lo] else lo
+    x_hi = hi - 1 + (s[hi - 1] - half) / (s[hi - 1] - s[hi]) if s[hi - 1] != s[hi] else hi
+    return peak, (x_hi - x_lo) * w
+
+
+def balance(sim, steps, every):
+    """Time-centred energy balance sampled along a run (two reads per sample)."""
+    out = []
+    done = 0
+    while done + every + 1 <= steps:
+        sim.step(every)
+        e0 = sim.energy()
+        sim.step(1)
+        e1 = sim.energy()
+        done += every + 1
+        out.append(e0[0] + 0.5 * (e0[1] + e1[1] + e0[2] + e1[2] + e0[3] + e1[3]) + e0[5] - e0[4])
+    if steps > done:
+        sim.step(steps - done)
+    return np.array(out), sim.energy()
+
+
+SMALL = dict(length_lambda=20, cells_per_lambda=200, cfl=0.95, lambda_um=0.8, rr_on=True, source_node=8)
+SMALL_STEPS = 4211
+N_SEEDS = 16
+
+
+def oracle_small_run(seed):
+    """One oracle run of the small single-run workload (process-pool worker)."""
+    import oracle as orc
+
+    o = orc.OracleSim(**SMALL)
+    o.load_foil(10.0, 1.0, 64.0, 1, 1.0, 64, seed)
+    o.inject_laser(200.0, orc.LP, orc.ENV_SIN2, 10.0)
+    o.step(SMALL_STEPS)
+    spec = o.spectra(orc.ION, 400, 0.0, 2000.0)[0]
+    e = o.energy()
+    o.close()
+    return spec, e
+
+
+def test_small_single_run_spectra_and_energy(picrr):
+    """Full runs are chaotic: single- and double-precision runs from the same
+    seed end as different as runs from different seeds, so spectra are
+    compared as ensembles of 16 seeds.  The oracle's own ensemble-to-ensemble
+    spread (two disjoint 8-seed ensembles, 95th percentile) is 5 % in the peak
+    and 11 % in the FWHM of this spectrum; a 16-seed ensemble halves that to
+    about 4 % and 8 %, the tolerances used here (2 % for the mean energy)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    seeds = list(range(1, N_SEEDS + 1))
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=min(N_SEEDS, os.cpu_count() or 4), mp_context=ctx) as ex:
+        fut = ex.map(oracle_small_run, seeds)
+        # energy bookkeeping on seed 1, GPU and oracle side by side
+        g = picrr.Sim(seed=1, sort_interval=8, **SMALL)
+        o = oracle.OracleSim(**SMALL)
+        g.load_foil(10.0, 1.0, 64.0, 1, 1.0, 64)
+        o.load_foil(10.0, 1.0, 64.0, 1, 1.0, 64, 1)
+        for s in (g, o):
+            s.inject_laser(200.0, picrr.LP, picrr.ENV_SIN2, 10.0)
+        bg, eg = balance(g, SMALL_STEPS, 199)
+        bo, eo = balance(o, SMALL_STEPS, 199)
+        g.close()
+        o.close()
+        u_in = eo[4]
+        assert u_in > 1e5 and eg[4] == pytest.approx(u_in, rel=1e-5)
+        assert np.max(np.abs(bo)) < 1e-3 * u_in
+        assert np.max(np.abs(bg)) < 1e-3 * u_in
+        assert np.max(np.abs(bg - bo)) < 1e-3 * u_in
+        spec_g, rad_g = 0.0, []
+        for seed in seeds:
+            g = picrr.Sim(seed=seed, sort_interval=8, **SMALL)
+            g.load_foil(10.0, 1.0, 64.0, 1, 1.0, 64)
+            g.inject_laser(200.0, picrr.LP, picrr.ENV_SIN2, 10.0)
+            g.step(SMALL_STEPS)
+            spec_g = spec_g + g.spectra(picrr.ION, 400, 0.0, 2000.0)[0]
+            rad_g.append(g.energy()[3])
+            g.close()
+        res = list(fut)
+    spec_o = sum(r[0] for r in res)
+    rad_o = [r[1][3] for r in res]
+    pg, fg = peak_fwhm(spec_g, 0.0, 2000.0)
+    po, fo = peak_fwhm(spec_o, 0.0, 2000.0)
+    assert po > 150.0  # the foil has been accelerated
+    assert pg == pytest.approx(po, rel=0.04), (pg, po)
+    assert fg == pytest.approx(fo, rel=0.08), (fg, fo)
+    e = (np.arange(400) + 0.5) * 5.0
+    assert (spec_g @ e) / spec_g.sum() == pytest.approx((spec_o @ e) / spec_o.sum(), rel=0.02)
+    assert np.mean(rad_g) == pytest.approx(np.mean(rad_o), rel=0.03)
+
+
+@pytest.mark.parametrize("a0,pol", [(350.0, 0)])
+def test_paper_scale_grid_first_500_steps(picrr, a0, pol):
+    kw = dict(length_lambda=60, cells_per_lambda=1000, cfl=0.95, lambda_um=0.8, rr_on=True, source_node=8)
+    g = picrr.Sim(seed=11, sort_interval=8, **kw)
+    o = oracle.OracleSim(**kw)
+    g.load_foil(0.1, 1.0, 90.0, 1, 1.0, 400)
+    o.load_foil(0.1, 1.0, 90.0, 1, 1.0, 400, 11)
+    # a 0.6-period sin^2 pulse peaks 0.3 periods (300 cells) behind its front,
+    # so its peak reaches the foil inside the 500-step window
+    for s in (g, o):
+        s.inject_laser(a0, pol, picrr.ENV_SIN2, 0.6)
+    g.step(500)
+    o.step(500)
+    for comps in ((picrr.EY, picrr.EZ), (picrr.BY, picrr.BZ), (picrr.EX,)):
+        a = np.concatenate([g.field(c) for c in comps])
+        b = np.concatenate([o.field(c) for c in comps])
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b), comps
+    pe_g, pe_o = g.particles(0), o.particles(0)
+    assert np.max(np.abs(pe_o["px"])) > 10.0
+    d = np.abs(pe_g["px"] - pe_o["px"]) / (1.0 + np.abs(pe_o["px"]))
+    assert np.median(d) < 1e-4
+
+
+def test_large_run_sampled_against_oracle(picrr):
+    # the benchmark's run and launch configuration
+    import bench
+
+    w = bench.LARGE
+    g = bench.make_sim(picrr, 0)
+    g.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
+    g.inject_laser(w["a0"], w["pol"], picrr.ENV_SIN2, w["duration"])
+    g.step(4000)  # the front reaches the foil after ~520 steps; 4000 steps: a ~ 0.07 a0 in it
+    fields = [g.field(c) for c in range(5)]
+    before = [g.particles(sp) for sp in (0, 1)]
+    g.step(1)
+    after = [g.particles(sp) for sp in (0, 1)]
+    nx, dx = g.nx, g.dx
+    assert len(before[0]["x"]) == 32_000_000
+    rng = np.random.default_rng(0)
+    kw = dict(length_lambda=w["length_lambda"], cells_per_lambda=w["cells_per_lambda"], cfl=w["cfl"],
+              lambda_um=w["lambda_um"], rr_on=w["rr_on"], source_node=w["source_node"])
+    o = oracle.OracleSim(**kw)
+    o.set_fields(*fields)
+    idx = {}
+    species = {0: (w["ne"] / w["ppc"], -1.0, 1.0), 1: (w["ne"] / w["ppc"], 1.0, 1836.15267343)}
+    for sp in (0, 1):
+        b = before[sp]
+        # sample: half uniformly, half among the most strongly driven particles
+        strong = np.argsort(-np.abs(b["px"]))[:10000]
+        pick = np.unique(np.concatenate([rng.choice(len(b["x"]), 10000, replace=False), strong]))
+        idx[sp] = pick
+        xi = b["x"][pick] / dx
+        cell = np.floor(xi).astype(np.int32)
+        off = xi - cell
+        o.load_particles(sp, cell, off, b["px"][pick], b["py"][pick], b["pz"][pick], *species[sp])
+    o.step(1)
+    for sp in (0, 1):
+        po = o.particles(sp)
+        a = after[sp]
+        pg = np.stack([a["px"][idx[sp]], a["py"][idx[sp]], a["pz"][idx[sp]]], 1)
+        pr = np.stack([po["px"], po["py"], po["pz"]], 1)
+        scale = np.maximum(np.linalg.norm(pr, axis=1), 1e-3 * w["a0"] * g.dt)
+        err = np.max(np.abs(pg - pr), axis=1) / scale
+        assert np.max(err) <= 1e-5, (sp, np.max(err))
+        assert np.max(np.abs(a["x"][idx[sp]] - po["x"])) <= 2e-6 * dx
+    # the laser is in the foil: skin-layer electrons carry transverse momentum
+    assert max(np.max(np.abs(before[0]["py"])), np.max(np.abs(before[0]["pz"]))) > 1.0
+    # Gauss's law on the whole grid after the step (all 64M particles)
+    rho = np.zeros(nx + 3)
+    for sp, q in ((0, -1.0), (1, 1.0)):
+        xi = after[sp]["x"] / dx
+        c = np.floor(xi).astype(np.int64)
+        f = xi - c
+        rho += q * species[sp][0] * (np.bincount(c, weights=1 - f, minlength=nx + 3)[: nx + 3]
+                                     + np.bincount(c + 1, weights=f, minlength=nx + 3)[: nx + 3])
+    ex = g.field(picrr.EX)
+    div = (ex[1:] - ex[:-1]) / dx
+    assert np.max(np.abs(div - rho[1:nx])) <= 1e-4 * np.max(np.abs(rho[: nx + 1]))

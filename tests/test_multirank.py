@@ -1,0 +1,45 @@
+"""The N > 1 host logic of bench.py on CPU: two gloo ranks aggregate their
+replicas' times (max) and work (sum) the way the GPU run does over NCCL."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    ms, total = bench.aggregate(torch, dist, 10.0 + 5.0 * rank, 1000.0 * (rank + 1))
+    out[rank] = (ms, total)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregate():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[0] == res[1] == (15.0, 3000.0)
+
+
+def test_single_rank_identity():
+    import bench
+
+    assert bench.aggregate(None, None, 7.0, 42.0) == (7.0, 42.0)
