@@ -191,6 +191,40 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything; NULL is accepted. */
 pic_status pic_destroy(pic_sim* sim);
 
+/* ---- Spectrum without device allocation -----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory when they need a spectrum:
+ * code that must not synchronise the GPU (cudaMalloc and cudaFree can), code
+ * whose device memory is owned by another allocator under a fixed budget, or
+ * a plugin that is handed device buffers by its host application.
+ *
+ * It computes what pic_spectra computes for one species, from momenta the
+ * caller already holds on the device, and allocates nothing: its integer bin
+ * counters live in one fixed array inside the library, sized for
+ * PIC_NOALLOC_MAX_BINS bins (plus under- and overflow, 8 bytes each, about
+ * 0.5 MB), which every GPU that loads the library keeps until the process
+ * exits.
+ *
+ *   px, py, pz   device arrays of n floats, momenta in m_s c (caller-owned)
+ *   mass_me      particle mass in electron masses (E = m c^2 (gamma - 1))
+ *   weight_dx    weight * dx of one macro-particle (the count unit)
+ *   counts       device array of nbins doubles (caller-owned), receives
+ *                weight_dx * (particles in bin k) / bin width, as pic_spectra
+ *   stream       cudaStream_t to run on (NULL: the legacy default stream)
+ *
+ * Runs on the current device, asynchronously on `stream`; the result is ready
+ * when the stream reaches it.  nbins outside [1, PIC_NOALLOC_MAX_BINS] is
+ * rejected with PIC_ERR_INVALID_ARG; pic_last_error(NULL) gives the reason.
+ * The first call on a device looks up the counter array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the counter array: each call
+ * clears it before counting, so calls in sequence are independent, but calls
+ * whose work overlaps on the GPU (other streams or threads) race on it. */
+#define PIC_NOALLOC_MAX_BINS 65536
+pic_status pic_spectrum_noalloc(const float* px, const float* py, const float* pz, int64_t n,
+                                double mass_me, double weight_dx, int nbins, double e_min_MeV,
+                                double e_max_MeV, double* counts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

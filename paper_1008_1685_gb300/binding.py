@@ -25,7 +25,9 @@ STATUS = {0: "PIC_OK", -1: "PIC_ERR_INVALID_ARG", -2: "PIC_ERR_STATE", -3: "PIC_
 SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles", "pic_load_particles_f32",
            "pic_set_fields",
            "pic_inject_laser", "pic_step_n", "pic_spectra", "pic_energy", "pic_read_particles",
-           "pic_read_fields", "pic_stats", "pic_set_timing", "pic_last_error", "pic_destroy")
+           "pic_read_fields", "pic_stats", "pic_set_timing", "pic_last_error", "pic_destroy",
+           "pic_spectrum_noalloc")
+NOALLOC_MAX_BINS = 65536
 
 
 class PicError(RuntimeError):
@@ -106,11 +108,23 @@ def library():
         L.pic_last_error.argtypes = [vp]
         L.pic_last_error.restype = C.c_char_p
         L.pic_destroy.argtypes = [vp]
+        L.pic_spectrum_noalloc.argtypes = [vp, vp, vp, i64, C.c_double, C.c_double, C.c_int, C.c_double,
+                                           C.c_double, vp, vp]
         for name in SYMBOLS:
             if name != "pic_last_error":
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
+
+
+def spectrum_noalloc(px_ptr, py_ptr, pz_ptr, n, mass_me, weight_dx, nbins, e_min, e_max, counts_ptr,
+                     stream_ptr=0):
+    """pic_spectrum_noalloc on device pointers (integers); returns the status
+    and, on failure, the library's message."""
+    L = library()
+    rc = L.pic_spectrum_noalloc(C.c_void_p(px_ptr), C.c_void_p(py_ptr), C.c_void_p(pz_ptr), n, mass_me,
+                                weight_dx, nbins, e_min, e_max, C.c_void_p(counts_ptr), C.c_void_p(stream_ptr))
+    return rc, (L.pic_last_error(None).decode() if rc else "")
 
 
 def _dp(a):

@@ -24,7 +24,7 @@ constexpr double kMpMe = 1836.15267343;      // proton mass / electron mass
 constexpr double kMuMe = 1822.888486209;     // atomic mass unit / electron mass
 constexpr int kMaxDiagBlocks = 1024;
 
-thread_local std::string g_create_error;
+thread_local std::string g_create_error;  // failures of calls without a handle
 
 struct HostSpecies {
     int64_t n = 0;
@@ -40,6 +40,10 @@ struct EventPair {
 };
 
 }  // namespace
+
+namespace picrr {
+void set_null_handle_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace picrr
 
 struct pic_sim {
     pic_config cfg{};

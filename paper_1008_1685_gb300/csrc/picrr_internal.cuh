@@ -187,6 +187,11 @@ void launch_build_units_from_sorted(const SortParams& S, cudaStream_t st, int* l
 
 void launch_foil(DevSpecies e, DevSpecies ion, int c0, int ncell, int ppc, uint64_t seed, cudaStream_t st);
 void launch_iota(int32_t* id, int64_t n, cudaStream_t st);
+}  // namespace picrr
+#include <string>
+namespace picrr {
+// record the message returned by pic_last_error(NULL) on this thread
+void set_null_handle_error(const std::string& msg);
 
 // Diagnostics.
 struct DiagParams {
