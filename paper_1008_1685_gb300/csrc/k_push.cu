@@ -5,9 +5,9 @@
 // whose cells at the last sort lie in one tile).  Because cfl < 1 a particle
 // moves less than one cell per step, so k steps after the sort every
 // particle of the unit lies in [lo - k, hi + k]; the CTA stages the fields of
-// the window [lo - k - 1, hi + k + 2] and the unit's particle arrays (SoA)
-// into shared memory with bulk TMA copies completing on one mbarrier,
-// updates the particles in place, writes them back with bulk TMA stores and
+// the window [lo - k - 1, hi + k + 2] into shared memory with one bulk TMA
+// copy per component (completing on one mbarrier), streams the particles
+// (structure of arrays) with 128-bit evict-first loads and stores, and
 // accumulates the unit's current in shared memory.
 //
 // Determinism: each particle's current is split into at most two "bin"
@@ -57,8 +57,7 @@ __device__ __forceinline__ float comp(const float4& a, int j) {
     return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
 }
 
-__global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) {
-    extern __shared__ __align__(128) unsigned char dsm[];  // particles of the unit: 5 x NPMAX words
+__global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) {
     __shared__ __align__(128) float sF[5][WMAX];
     __shared__ __align__(16) unsigned long long sJ[NQ][WMAX];
     __shared__ __align__(8) uint64_t bar;
@@ -88,23 +87,13 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
     }
     __syncthreads();
     const DevSpecies sp = P.sp[s];
-    // the unit's particles, from the aligned slot before `start` to the aligned
-    // slot after `end` (at most 3 particles of each neighbour, never written here)
+    // the unit's particles are read in 16-byte slots of 4, from the aligned slot
+    // before `start` to the aligned slot after `end`; the at most 3 particles
+    // of each neighbouring unit in those slots are never written here
     const int base = start & ~3;
-    const int np4 = ((end + 3) & ~3) - base;  // <= UNIT_P + 6, a multiple of 4
-    int32_t* sC = reinterpret_cast<int32_t*>(dsm);
-    float* sO = reinterpret_cast<float*>(dsm) + NPMAX;
-    float* sX = sO + NPMAX;
-    float* sY = sX + NPMAX;
-    float* sZ = sY + NPMAX;
+    const int np4 = ((end + 3) & ~3) - base;
     if (tid == 0) {
-        const uint32_t pb = static_cast<uint32_t>(np4) * 4u;
-        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u + 5u * pb);
-        tma_load_1d(sC, sp.cell + base, pb, &bar);
-        tma_load_1d(sO, sp.off + base, pb, &bar);
-        tma_load_1d(sX, sp.px + base, pb, &bar);
-        tma_load_1d(sY, sp.py + base, pb, &bar);
-        tma_load_1d(sZ, sp.pz + base, pb, &bar);
+        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
 #pragma unroll
         for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], P.F[c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
     }
@@ -131,8 +120,7 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
     float rad = 0.f;
     int rk = -1;  // running old-bin record of this thread
     float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f;
-    int rk2 = -1;  // running new-bin record
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;
+
     for (int r = 0; r < rounds; ++r) {
         const int slot = r * PUSH_T + tid;
         const int b4 = base + 4 * slot;
@@ -140,11 +128,11 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
         int4 c4 = make_int4(-1, -1, -1, -1);
         float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = o4, y4 = o4, z4 = o4;
         if (slot_ok) {
-            c4 = reinterpret_cast<const int4*>(sC)[slot];
-            o4 = reinterpret_cast<const float4*>(sO)[slot];
-            x4 = reinterpret_cast<const float4*>(sX)[slot];
-            y4 = reinterpret_cast<const float4*>(sY)[slot];
-            z4 = reinterpret_cast<const float4*>(sZ)[slot];
+            c4 = __ldcs(reinterpret_cast<const int4*>(sp.cell + b4));
+            o4 = __ldcs(reinterpret_cast<const float4*>(sp.off + b4));
+            x4 = __ldcs(reinterpret_cast<const float4*>(sp.px + b4));
+            y4 = __ldcs(reinterpret_cast<const float4*>(sp.py + b4));
+            z4 = __ldcs(reinterpret_cast<const float4*>(sp.pz + b4));
         }
         int cn[4];
         float fo[4], qx[4], qy[4], qz[4];
@@ -286,23 +274,7 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
                 r3 += vo3;
                 r4 += vo4;
             }
-            // new-bin records (boundary crossings) go to a second running record
-            const bool merge2 = kn < 0 || rk2 < 0 || kn == rk2;
-            if (__any_sync(FULL, !merge2)) {
-                warp_add(merge2 ? -1 : rk2, q0, q1, q2, q3, q4, sJ, lscale, shift);
-                if (!merge2) {
-                    rk2 = -1;
-                    q0 = q1 = q2 = q3 = q4 = 0.f;
-                }
-            }
-            if (kn >= 0) {
-                rk2 = kn;
-                q0 += vn0;
-                q1 += vn1;
-                q2 += vn2;
-                q3 += vn3;
-                q4 += vn4;
-            }
+            if (__any_sync(FULL, kn >= 0)) warp_add(kn, vn0, vn1, vn2, vn3, vn4, sJ, lscale, shift);
             act[j] = a;
             cn[j] = c;
             fo[j] = f;
@@ -310,48 +282,31 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
             qy[j] = py;
             qz[j] = pz;
         }
-        if (slot_ok) {  // results back in place; the CTA writes them to global memory below
-            reinterpret_cast<int4*>(sC)[slot] = make_int4(cn[0], cn[1], cn[2], cn[3]);
-            reinterpret_cast<float4*>(sO)[slot] = make_float4(fo[0], fo[1], fo[2], fo[3]);
-            reinterpret_cast<float4*>(sX)[slot] = make_float4(qx[0], qx[1], qx[2], qx[3]);
-            reinterpret_cast<float4*>(sY)[slot] = make_float4(qy[0], qy[1], qy[2], qy[3]);
-            reinterpret_cast<float4*>(sZ)[slot] = make_float4(qz[0], qz[1], qz[2], qz[3]);
+        warp_add(rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
+        rk = -1;
+        r0 = r1 = r2 = r3 = r4 = 0.f;
+        if (slot_ok) {
+            if (b4 >= start && b4 + 3 < end) {
+                __stcs(reinterpret_cast<int4*>(sp.cell + b4), make_int4(cn[0], cn[1], cn[2], cn[3]));
+                __stcs(reinterpret_cast<float4*>(sp.off + b4), make_float4(fo[0], fo[1], fo[2], fo[3]));
+                __stcs(reinterpret_cast<float4*>(sp.px + b4), make_float4(qx[0], qx[1], qx[2], qx[3]));
+                __stcs(reinterpret_cast<float4*>(sp.py + b4), make_float4(qy[0], qy[1], qy[2], qy[3]));
+                __stcs(reinterpret_cast<float4*>(sp.pz + b4), make_float4(qz[0], qz[1], qz[2], qz[3]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (!act[j]) continue;
+                    sp.cell[b4 + j] = cn[j];
+                    sp.off[b4 + j] = fo[j];
+                    sp.px[b4 + j] = qx[j];
+                    sp.py[b4 + j] = qy[j];
+                    sp.pz[b4 + j] = qz[j];
+                }
+            }
         }
     }
 
-    // write the unit back: the 16-byte aligned interior with bulk TMA stores,
-    // the at most 3 + 3 particles at the ends (which share an aligned slot
-    // with a neighbouring unit) with plain stores
-    const int s4 = (start + 3) & ~3, e4 = end & ~3;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && e4 > s4) {
-        const uint32_t b = static_cast<uint32_t>(e4 - s4) * 4u, o = static_cast<uint32_t>(s4 - base);
-        tma_store_1d(sp.cell + s4, sC + o, b);
-        tma_store_1d(sp.off + s4, sO + o, b);
-        tma_store_1d(sp.px + s4, sX + o, b);
-        tma_store_1d(sp.py + s4, sY + o, b);
-        tma_store_1d(sp.pz + s4, sZ + o, b);
-        tma_store_commit();
-    }
-    if (tid < 8) {
-        const int h_end = min(s4, end), t_beg = max(e4, s4);
-        const int i = tid < 4 ? start + tid : t_beg + (tid - 4);
-        const bool ok = tid < 4 ? i < h_end : i < end;
-        if (ok) {
-            const int o = i - base;
-            sp.cell[i] = sC[o];
-            sp.off[i] = sO[o];
-            sp.px[i] = sX[o];
-            sp.py[i] = sY[o];
-            sp.pz[i] = sZ[o];
-        }
-    }
 
-    // a thread holds at most 12 particles of a unit (UNIT_P / PUSH_T + 4), so a
-    // running record stays below 16 particles: |record| < 2^26 / 32 per lane
-    warp_add(rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
-    if (__any_sync(FULL, rk2 >= 0)) warp_add(rk2, q0, q1, q2, q3, q4, sJ, lscale, shift);
 
     // radiated energy of the unit: fixed-order warp reduction, warps summed in double
 #pragma unroll
@@ -372,20 +327,13 @@ __global__ void __launch_bounds__(PUSH_T, 3) k_push_deposit(const PushParams P) 
         if (jy) atomicAdd(P.J[1] + p0 + i, jy);
         if (jz) atomicAdd(P.J[2] + p0 + i, jz);
     }
-    if (tid == 0) tma_store_wait_read();  // shared memory must outlive the bulk stores' reads
 }
 
 }  // namespace
 
 void launch_push(const PushParams& P, int grid, cudaStream_t st) {
     if (grid <= 0) return;
-    constexpr size_t dyn = 5u * NPMAX * 4u;
-    static bool attr = false;  // per process; the attribute is per function and device-independent
-    if (!attr) {
-        cudaFuncSetAttribute(k_push_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-        attr = true;
-    }
-    k_push_deposit<<<grid, PUSH_T, dyn, st>>>(P);
+    k_push_deposit<<<grid, PUSH_T, 0, st>>>(P);
 }
 
 }  // namespace picrr

@@ -24,7 +24,6 @@ constexpr int TILE = 64;          // cells per tile: bounds the cell span of a u
 constexpr int UNIT_P = 2048;      // particles per unit at most
 constexpr int KMAX = 32;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
-constexpr int NPMAX = UNIT_P + 8;  // particle slots of a unit staged in shared memory (multiple of 4)
 constexpr int WMAX = 144;         // window length bound in the push kernel (>= TILE + 2 KMAX + 10)
 constexpr int SSTR = TILE + 2 * KMAX + 4;  // per-unit key-window stride of the sort scratch
 constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
@@ -141,19 +140,6 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
             smem_u32(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
-}
-
-// 1D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
-// from this CTA's shared memory to global memory, in the current bulk group.
-__device__ __forceinline__ void tma_store_1d(void* dst_gmem, const void* src_smem, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
-                 "r"(smem_u32(src_smem)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// Wait until every committed bulk store has finished reading shared memory.
-__device__ __forceinline__ void tma_store_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
