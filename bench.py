@@ -41,6 +41,186 @@ LARGE = dict(length_lambda=100.0, cells_per_lambda=2000.0, cfl=0.95, lambda_um=0
              duration=20.0, seed=4, sort_interval=8)
 BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int32 + 4 x fp32)
 
+# the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
+# 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
+SCAN = dict(n_runs=256, length_lambda=30.0, cells_per_lambda=500.0, cfl=0.95, foil_x0=10.0, periods=40.0,
+            duration=20.0, seed_base=1000, sort_interval=8)
+
+
+def scan_steps(periods, w=SCAN):
+    return int(math.ceil(periods * w["cells_per_lambda"] / w["cfl"] - 1e-9))
+
+
+def scan_desc(i, w=SCAN):
+    """Parameters of scan run i, drawn from seed base + i: a0 ~ U[100, 600],
+    thickness ~ U[0.5, 2] lambda, n_e ~ U[30, 150] n_c, LP/CP and RR on/off at
+    50/50, particles per cell ~ U{32..256}."""
+    import numpy as np
+
+    rng = np.random.default_rng(w["seed_base"] + i)
+    return dict(length_lambda=w["length_lambda"], foil_x0=w["foil_x0"], foil_thickness=float(rng.uniform(0.5, 2.0)),
+                ne=float(rng.uniform(30.0, 150.0)), a0=float(rng.uniform(100.0, 600.0)),
+                polarization=int(rng.integers(0, 2)), rr_on=bool(rng.integers(0, 2)), ppc=int(rng.integers(32, 257)),
+                duration=w["duration"], steps=scan_steps(w["periods"], w), seed=w["seed_base"] + i)
+
+
+def desc_particles(d, cpl):
+    return 2 * d["ppc"] * int(round(d["foil_thickness"] * cpl))
+
+
+# the served request stream: Poisson arrivals, sizes log-uniform in 1e4..1e6
+# particles per species, 20..200 periods, physical parameters as in the scan,
+# admission by device memory under a 150 GB budget
+SERVE = dict(rate=20.0, window_s=10.0, cap_s=45.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77)
+
+
+def serve_requests(rate, window_s, seed, w=SCAN):
+    """Arrival times (s) and run descriptions of the request stream."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out, t, i = [], 0.0, 0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= window_s:
+            return out
+        n = math.exp(rng.uniform(math.log(1e4), math.log(1e6)))
+        thick = float(rng.uniform(0.5, 2.0))
+        ppc = max(1, int(round(n / (thick * w["cells_per_lambda"]))))
+        periods = float(rng.uniform(20.0, 200.0))
+        d = dict(length_lambda=w["length_lambda"], foil_x0=w["foil_x0"], foil_thickness=thick,
+                 ne=float(rng.uniform(30.0, 150.0)), a0=float(rng.uniform(100.0, 600.0)),
+                 polarization=int(rng.integers(0, 2)), rr_on=bool(rng.integers(0, 2)), ppc=ppc,
+                 duration=w["duration"], steps=scan_steps(periods, w), seed=seed * 100000 + i)
+        out.append((t, d))
+        i += 1
+
+
+def _latency_summary(lat, pending_ages, elapsed, n_req):
+    import numpy as np
+
+    done = np.array(sorted(lat)) if lat else np.zeros(0)
+    cens = np.array(sorted(list(lat) + list(pending_ages)))
+    q = lambda a, p: float(np.percentile(a, p)) if len(a) else None
+    return {"requests": n_req, "completed": len(lat), "unfinished": len(pending_ages),
+            "p50_s": q(done, 50), "p99_s": q(done, 99),
+            "p50_s_with_unfinished_lower_bound": q(cens, 50), "p99_s_with_unfinished_lower_bound": q(cens, 99),
+            "runs_per_hour": 3600.0 * len(lat) / elapsed}
+
+
+def serve_leg(picrr, device, cfg=SERVE, w=SCAN):
+    """Continuous batching through pic_server: requests are submitted at their
+    arrival times; latency = submission to spectra on the host."""
+    import threading
+
+    reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    srv = picrr.Server(w["cells_per_lambda"], max_runs=cfg["max_runs"], chunk_steps=cfg["chunk"], cfl=w["cfl"],
+                       sort_interval=w["sort_interval"], device=device, hbm_budget_bytes=cfg["budget"])
+    tickets = []
+    t0 = time.perf_counter()
+
+    def submitter():
+        for ta, d in reqs:
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append((ta, srv.submit(nbins=200, ion_e_max=2000.0, el_e_max=2000.0, **d)))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, done = [], set()
+    while time.perf_counter() - t0 < cfg["cap_s"]:
+        for ta, t in list(tickets):
+            if t not in done:
+                r = srv.result(t, 0.0)
+                if r is not None:
+                    lat.append(r["latency_s"])
+                    done.add(t)
+        if len(done) == len(reqs):
+            break
+        time.sleep(0.01)
+    th.join()
+    el = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    pending = [el - ta for ta, t in tickets if t not in done]
+    out = _latency_summary(lat, pending, el, len(reqs))
+    work = sum(desc_particles(d, w["cells_per_lambda"]) * d["steps"] for _, d in reqs)
+    out.update(elapsed_s=el, offered_particle_steps_per_s=work / cfg["window_s"],
+               served_particle_steps_per_s=st["particle_steps"] / el,
+               peak_device_bytes=st["peak_device_bytes"], batch_steps=st["batch_steps"])
+    return out
+
+
+def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
+    """The same request stream served one run at a time in arrival order
+    through the single-run API (no batching), under the same time cap."""
+    reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    t0 = time.perf_counter()
+    lat, i = [], 0
+    while i < len(reqs) and time.perf_counter() - t0 < cfg["cap_s"]:
+        ta, d = reqs[i]
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
+                      sort_interval=w["sort_interval"], seed=d["seed"], device=device)
+        s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        s.inject_laser(d["a0"], d["polarization"], 0, d["duration"])
+        left = d["steps"]
+        while left > 0 and time.perf_counter() - t0 < cfg["cap_s"]:
+            left -= s.step(min(left, 4096))
+        if left == 0:
+            s.spectra(1, 200, 0.0, 2000.0)
+            s.spectra(0, 200, 0.0, 2000.0)
+            s.energy()
+            lat.append(time.perf_counter() - t0 - ta)
+            i += 1
+        s.close()
+    el = time.perf_counter() - t0
+    arrived = [ta for ta, _ in reqs[i:] if ta <= el]
+    return _latency_summary(lat, [el - ta for ta in arrived], el, len(reqs))
+
+
+def batched_scan(picrr, device, n_runs, w=SCAN):
+    """All runs in one batch (one launch per kernel per step for all of them),
+    from creation to every run's ion spectrum on the host."""
+    descs = [scan_desc(i, w) for i in range(n_runs)]
+    t0 = time.perf_counter()
+    b = picrr.Batch(w["cells_per_lambda"], max_runs=n_runs, cfl=w["cfl"], sort_interval=w["sort_interval"],
+                    device=device)
+    ids = [b.add_run(d["length_lambda"], d["foil_x0"], d["foil_thickness"], d["ne"], d["a0"], d["polarization"],
+                     d["duration"], d["steps"], rr_on=d["rr_on"], ppc=d["ppc"], seed=d["seed"]) for d in descs]
+    while b.step(4096) > 0:
+        pass
+    for r in ids:
+        b.spectra(r, 1, 200, 0.0, 2000.0)
+    el = time.perf_counter() - t0
+    st = b.stats()
+    b.close()
+    ps = sum(desc_particles(d, w["cells_per_lambda"]) * d["steps"] for d in descs)
+    return dict(runs=n_runs, seconds=el, runs_per_hour=3600.0 * n_runs / el, particle_steps_per_s=ps / el,
+                particles=sum(desc_particles(d, w["cells_per_lambda"]) for d in descs),
+                push_launches=st["push_launches"], kernel_launches=st["kernel_launches"])
+
+
+def plain_scan(picrr, device, n_runs, w=SCAN):
+    """The same runs one at a time through the single-run API (create, foil,
+    laser, step to the end, ion spectrum, destroy), on the same GPU."""
+    descs = [scan_desc(i, w) for i in range(n_runs)]
+    t0 = time.perf_counter()
+    for d in descs:
+        s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
+                      sort_interval=w["sort_interval"], seed=d["seed"], device=device)
+        s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        s.inject_laser(d["a0"], d["polarization"], 0, d["duration"])
+        s.step(d["steps"])
+        s.spectra(1, 200, 0.0, 2000.0)
+        s.close()
+    el = time.perf_counter() - t0
+    ps = sum(desc_particles(d, w["cells_per_lambda"]) * d["steps"] for d in descs)
+    return dict(runs=n_runs, seconds=el, runs_per_hour=3600.0 * n_runs / el, particle_steps_per_s=ps / el)
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -206,6 +386,13 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=40)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scan-runs", type=int, default=SCAN["n_runs"], help="runs of the batched scan (0: skip)")
+    ap.add_argument("--plain-runs", type=int, default=8,
+                    help="runs of the scan stepped one at a time for the plain comparison (0: skip)")
+    ap.add_argument("--serve-window", type=float, default=SERVE["window_s"],
+                    help="seconds of request arrivals of the serving leg (0: skip)")
+    ap.add_argument("--serve-cap", type=float, default=SERVE["cap_s"], help="time cap of each serving arm (s)")
+    ap.add_argument("--serve-rate", type=float, default=SERVE["rate"], help="request arrivals per second")
     ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
                     help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
@@ -274,6 +461,32 @@ def main():
                "what": "pic_create + pic_load_particles_f32 from pinned host SoA + pic_inject_laser + "
                        "pic_step_n(steps) + pic_spectra + pic_energy, host wall clock"}
 
+    scan = None
+    if args.scan_runs > 0:
+        scan = batched_scan(picrr, local, args.scan_runs)
+        if args.plain_runs > 0:
+            plain = plain_scan(picrr, local, min(args.plain_runs, args.scan_runs))
+            scan["plain"] = plain
+            scan["speedup_runs_per_hour"] = scan["runs_per_hour"] / plain["runs_per_hour"]
+        scan["workload"] = ("%d runs, 15,000 cells (30 lambda, lambda/500), 21,053 steps each; a0 U[100,600], "
+                            "thickness U[0.5,2] lambda, n_e U[30,150] n_c, LP/CP, RR on/off, ppc U{32..256}; "
+                            "plain = the first %d of the same runs one at a time" % (args.scan_runs, args.plain_runs))
+        ms_scan, _ = aggregate(torch, dist, scan["seconds"] * 1e3, 0.0)
+        scan["runs_per_hour"] = 3600.0 * args.scan_runs * ws / (ms_scan / 1e3)
+
+    serving = None
+    if args.serve_window > 0:
+        cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate)
+        serving = serve_leg(picrr, local, cfg)
+        serving["plain"] = plain_serve_leg(picrr, local, cfg)
+        serving["overloaded"] = serving["offered_particle_steps_per_s"] > serving["served_particle_steps_per_s"]
+        serving["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
+                               "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
+                               "the scan; 150 GB admission budget, %d slots, %d-step chunks; each arm capped at %g s; "
+                               "latency = submission to ion + electron spectra on the host"
+                               % (cfg["rate"], cfg["window_s"], cfg["seed"], cfg["max_runs"], cfg["chunk"],
+                                  cfg["cap_s"]))
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, sample = oracle_sample(args.ref_steps)
@@ -298,6 +511,8 @@ def main():
             "step_breakdown_ms": {"push": st1["push_ms"] / args.steps, "field": st1["field_ms"] / args.steps,
                                   "sort": st1["sort_ms"] / args.steps},
             "runs_per_hour": 3600.0 / (2000 * ms_max / args.steps / 1e3) * ws,
+            "batched_scan": scan,
+            "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -191,6 +191,118 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything; NULL is accepted. */
 pic_status pic_destroy(pic_sim* sim);
 
+/* ---- Batches of independent runs ---------------------------------------------
+ * A batch steps many independent runs together: every kernel of a step is
+ * one launch for all active runs of the batch, so small runs share the GPU
+ * instead of each leaving most of it idle.  All runs of a batch share the
+ * grid resolution, cfl, wavelength and sort interval of the batch's
+ * pic_config (its length_lambda, rr_on, seed and source_node are unused);
+ * everything else is per run.  Each run gives the same results alone and in
+ * a batch (up to single-precision rounding: the batch changes no arithmetic
+ * of a run, only how its work is packed into launches).  A pic_sim handle is
+ * a batch of one run. */
+typedef struct pic_batch pic_batch;
+
+/* One run: box, foil (as pic_load_foil), laser (as pic_inject_laser), length. */
+typedef struct {
+    double length_lambda;  /* box length in wavelengths */
+    int source_node;       /* laser injection node, 0 selects 8 */
+    int rr_on;             /* radiation reaction on electrons */
+    uint64_t seed;         /* foil loader seed */
+    double foil_x0_lambda, foil_thickness_lambda, ne_over_nc;
+    int ion_Z;
+    double ion_A;
+    int ppc;
+    double a0;
+    int polarization, envelope;
+    double duration_periods, rise_periods;
+    int64_t steps;         /* the run stops after this many steps (>= 1) */
+} pic_run_desc;
+
+/* Batch with room for max_runs runs (1..65536) on common->device. */
+pic_status pic_batch_create(const pic_config* common, int max_runs, pic_batch** out);
+/* As pic_set_stream. */
+pic_status pic_batch_set_stream(pic_batch* batch, void* cuda_stream);
+/* Add a run (allocates its grid and particles, generates its foil).  It joins
+ * the batch at the next pic_batch_step, at a sort boundary (the batch sorts
+ * early if needed).  *run_id receives its slot.  PIC_ERR_OOM if the budget is
+ * exceeded (the batch is unchanged); PIC_ERR_STATE if all slots are used. */
+pic_status pic_batch_add_run(pic_batch* batch, const pic_run_desc* desc, int* run_id);
+/* Advance every active run by up to n steps; a run stops when it reaches its
+ * own step count.  *steps_done (nullable) receives the batch steps taken (0
+ * when no run is active).  Synchronous. */
+pic_status pic_batch_step(pic_batch* batch, int64_t n, int64_t* steps_done);
+/* Steps completed by a run and whether it has finished. */
+pic_status pic_batch_run_status(pic_batch* batch, int run, int64_t* steps_done, int* finished);
+/* Per-run read-outs, as pic_energy / pic_spectra / pic_read_particles / pic_read_fields. */
+pic_status pic_batch_energy(pic_batch* batch, int run, double out[6]);
+pic_status pic_batch_spectra(pic_batch* batch, int run, int species, int nbins, double e_min_MeV,
+                             double e_max_MeV, double* counts, double* radiated_J_per_m2);
+pic_status pic_batch_read_particles(pic_batch* batch, int run, int species, int64_t cap, double* x,
+                                    double* px, double* py, double* pz, int32_t* flag, int64_t* n);
+pic_status pic_batch_read_fields(pic_batch* batch, int run, int comp, int64_t cap, double* out, int64_t* n);
+/* Free a finished run's device memory; its slot can take a new run. */
+pic_status pic_batch_release_run(pic_batch* batch, int run);
+/* Device bytes the run described by desc would take in this batch: its grid,
+ * sort scratch and both particle buffers, plus its share of the batch's work
+ * unit table with that table's growth headroom.  No allocation; used for
+ * admission by memory.  Reads only the batch's configuration, so it may be
+ * called from any thread; its error message is pic_batch_last_error(NULL). */
+pic_status pic_batch_run_footprint(const pic_batch* batch, const pic_run_desc* desc, size_t* bytes);
+pic_status pic_batch_stats(pic_batch* batch, pic_stats_t* out);
+pic_status pic_batch_set_timing(pic_batch* batch, int on);
+const char* pic_batch_last_error(const pic_batch* batch);
+pic_status pic_batch_destroy(pic_batch* batch);
+
+/* ---- Serving: a request loop over a batch --------------------------------
+ * A server owns one batch and one worker thread.  Run requests are queued
+ * when submitted and admitted in arrival order while a batch slot is free and
+ * the run's footprint (pic_batch_run_footprint) fits the device-memory
+ * budget (hbm_budget_bytes of the pic_config; 0: no budget).  Admitted runs
+ * join the running batch between step chunks (continuous batching: a request
+ * that arrives while others are stepping starts without waiting for them),
+ * stay resident on the device until their last step, and the worker then
+ * computes their ion and electron spectra and energy read-outs, frees their
+ * memory and admits more.  Results stay in the server until fetched.
+ * Each result is the same as that of the run stepped alone (see the batch
+ * above).  All calls are thread-safe. */
+typedef struct pic_server pic_server;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t queued, running;      /* now */
+    int64_t batch_steps;          /* steps taken by the batch */
+    int64_t particle_steps;       /* particles pushed, summed over steps and runs */
+    double busy_s;                /* worker wall time spent stepping */
+    int64_t device_bytes;         /* now */
+    int64_t peak_device_bytes;    /* highest after an admission */
+} pic_server_stats_t;
+
+/* common: grid resolution, cfl, wavelength, sort interval, device, budget (as
+ * pic_batch_create).  max_runs: batch slots.  chunk_steps (>= 1, rounded up to
+ * a multiple of the sort interval): steps between admission points. */
+pic_status pic_server_create(const pic_config* common, int max_runs, int64_t chunk_steps, pic_server** out);
+/* Queue a run.  Its results: the ion and electron spectra dN/dE over nbins
+ * equal bins of [0, ion_e_max_MeV) and [0, el_e_max_MeV), and the energy
+ * read-out of pic_energy, all at the run's last step.  *ticket identifies the
+ * request.  PIC_ERR_OOM if the run alone exceeds the budget;
+ * PIC_ERR_INVALID_ARG for an invalid description (checked as
+ * pic_batch_add_run checks it, at admission: the request then fails). */
+pic_status pic_server_submit(pic_server* srv, const pic_run_desc* desc, int nbins, double ion_e_max_MeV,
+                             double el_e_max_MeV, int64_t* ticket);
+/* Wait up to wait_s seconds (0: do not wait) for a request.  PIC_OK: the
+ * outputs (caller-owned ion_counts[nbins], el_counts[nbins], energy[6]; each
+ * nullable) and *latency_s (submission to result) are written and the ticket
+ * is forgotten.  PIC_ERR_TIMEOUT: not finished yet.  A request that failed
+ * returns its error (and is forgotten).  PIC_ERR_INVALID_ARG: unknown ticket. */
+pic_status pic_server_result(pic_server* srv, int64_t ticket, double wait_s, double* ion_counts, double* el_counts,
+                             double* energy, double* latency_s);
+pic_status pic_server_stats(pic_server* srv, pic_server_stats_t* out);
+/* Message of the last failed server call of the calling thread. */
+const char* pic_server_last_error(const pic_server* srv);
+/* Stop the worker (unfinished requests are dropped) and free everything. */
+pic_status pic_server_destroy(pic_server* srv);
+
 /* ---- Spectrum without device allocation -----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory when they need a spectrum:

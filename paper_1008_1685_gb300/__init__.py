@@ -8,5 +8,5 @@ CPU fallback, and importing the binding raises if the library is missing.
 """
 from .binding import (  # noqa: F401
     BY, BZ, CP, ELECTRON, ENV_SIN2, ENV_TRAPEZOID, EX, EY, EZ, ION, JX, JY, JZ, LP,
-    PicError, Sim, Stats, library, library_path,
+    Batch, PicError, RunDesc, Server, ServerStats, Sim, Stats, library, library_path, run_desc,
 )

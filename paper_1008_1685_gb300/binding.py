@@ -26,7 +26,12 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_set_fields",
            "pic_inject_laser", "pic_step_n", "pic_spectra", "pic_energy", "pic_read_particles",
            "pic_read_fields", "pic_stats", "pic_set_timing", "pic_last_error", "pic_destroy",
-           "pic_spectrum_noalloc")
+           "pic_spectrum_noalloc", "pic_batch_create", "pic_batch_set_stream", "pic_batch_add_run",
+           "pic_batch_step", "pic_batch_run_status", "pic_batch_energy", "pic_batch_spectra",
+           "pic_batch_read_particles", "pic_batch_read_fields", "pic_batch_release_run", "pic_batch_stats",
+           "pic_batch_set_timing", "pic_batch_last_error", "pic_batch_destroy", "pic_batch_run_footprint",
+           "pic_server_create", "pic_server_submit", "pic_server_result", "pic_server_stats",
+           "pic_server_last_error", "pic_server_destroy")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -49,6 +54,36 @@ class Config(C.Structure):
         ("source_node", C.c_int),
         ("hbm_budget_bytes", C.c_size_t),
     ]
+
+
+class RunDesc(C.Structure):
+    _fields_ = [
+        ("length_lambda", C.c_double),
+        ("source_node", C.c_int),
+        ("rr_on", C.c_int),
+        ("seed", C.c_uint64),
+        ("foil_x0_lambda", C.c_double),
+        ("foil_thickness_lambda", C.c_double),
+        ("ne_over_nc", C.c_double),
+        ("ion_Z", C.c_int),
+        ("ion_A", C.c_double),
+        ("ppc", C.c_int),
+        ("a0", C.c_double),
+        ("polarization", C.c_int),
+        ("envelope", C.c_int),
+        ("duration_periods", C.c_double),
+        ("rise_periods", C.c_double),
+        ("steps", C.c_int64),
+    ]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "admitted", "completed", "failed", "queued", "running",
+                                          "batch_steps", "particle_steps")] + \
+               [("busy_s", C.c_double), ("device_bytes", C.c_int64), ("peak_device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -110,8 +145,32 @@ def library():
         L.pic_destroy.argtypes = [vp]
         L.pic_spectrum_noalloc.argtypes = [vp, vp, vp, i64, C.c_double, C.c_double, C.c_int, C.c_double,
                                            C.c_double, vp, vp]
+        L.pic_batch_create.argtypes = [C.POINTER(Config), C.c_int, C.POINTER(vp)]
+        L.pic_batch_set_stream.argtypes = [vp, vp]
+        L.pic_batch_add_run.argtypes = [vp, C.POINTER(RunDesc), C.POINTER(C.c_int)]
+        L.pic_batch_step.argtypes = [vp, i64, C.POINTER(i64)]
+        L.pic_batch_run_status.argtypes = [vp, C.c_int, C.POINTER(i64), C.POINTER(C.c_int)]
+        L.pic_batch_energy.argtypes = [vp, C.c_int, dp]
+        L.pic_batch_spectra.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp]
+        L.pic_batch_read_particles.argtypes = [vp, C.c_int, C.c_int, i64, dp, dp, dp, dp, C.POINTER(C.c_int32),
+                                               C.POINTER(i64)]
+        L.pic_batch_read_fields.argtypes = [vp, C.c_int, C.c_int, i64, dp, C.POINTER(i64)]
+        L.pic_batch_release_run.argtypes = [vp, C.c_int]
+        L.pic_batch_stats.argtypes = [vp, C.POINTER(Stats)]
+        L.pic_batch_set_timing.argtypes = [vp, C.c_int]
+        L.pic_batch_last_error.argtypes = [vp]
+        L.pic_batch_last_error.restype = C.c_char_p
+        L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_run_footprint.argtypes = [vp, C.POINTER(RunDesc), C.POINTER(C.c_size_t)]
+        L.pic_server_create.argtypes = [C.POINTER(Config), C.c_int, i64, C.POINTER(vp)]
+        L.pic_server_submit.argtypes = [vp, C.POINTER(RunDesc), C.c_int, C.c_double, C.c_double, C.POINTER(i64)]
+        L.pic_server_result.argtypes = [vp, i64, C.c_double, dp, dp, dp, dp]
+        L.pic_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.pic_server_last_error.argtypes = [vp]
+        L.pic_server_last_error.restype = C.c_char_p
+        L.pic_server_destroy.argtypes = [vp]
         for name in SYMBOLS:
-            if name != "pic_last_error":
+            if name not in ("pic_last_error", "pic_batch_last_error", "pic_server_last_error"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -247,3 +306,174 @@ class Sim:
 
     def set_timing(self, on=True):
         self._check(self._L.pic_set_timing(self._h, int(on)))
+
+
+def run_desc(length_lambda, foil_x0, foil_thickness, ne, a0, polarization, duration, steps, rr_on=True, ppc=64,
+             ion_Z=1, ion_A=1.0, envelope=ENV_SIN2, rise=0.0, seed=1, source_node=8):
+    return RunDesc(length_lambda, source_node, int(rr_on), seed, foil_x0, foil_thickness, ne, ion_Z, ion_A, ppc,
+                   a0, polarization, envelope, duration, rise, steps)
+
+
+class Batch:
+    """Many independent runs stepped together (pic_batch_*)."""
+
+    def __init__(self, cells_per_lambda, max_runs, cfl=0.95, lambda_um=0.8, sort_interval=8, device=0,
+                 hbm_budget_bytes=0):
+        self._L = library()
+        cfg = Config(1.0, cells_per_lambda, cfl, lambda_um, 1, sort_interval, 0, device, 0, hbm_budget_bytes)
+        h = C.c_void_p()
+        rc = self._L.pic_batch_create(C.byref(cfg), max_runs, C.byref(h))
+        if rc != 0:
+            raise PicError(rc, self._L.pic_batch_last_error(None).decode())
+        self._h = h
+        self.dx = 2 * np.pi / cells_per_lambda
+        self.dt = cfl * self.dx
+        self.cells_per_lambda = cells_per_lambda
+        self._nx = {}
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PicError(rc, self._L.pic_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pic_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._check(self._L.pic_batch_set_stream(self._h, C.c_void_p(stream_ptr)))
+
+    def add_run(self, length_lambda, foil_x0, foil_thickness, ne, a0, polarization, duration, steps, rr_on=True,
+                ppc=64, ion_Z=1, ion_A=1.0, envelope=ENV_SIN2, rise=0.0, seed=1, source_node=8):
+        d = run_desc(length_lambda, foil_x0, foil_thickness, ne, a0, polarization, duration, steps, rr_on, ppc,
+                     ion_Z, ion_A, envelope, rise, seed, source_node)
+        rid = C.c_int(-1)
+        self._check(self._L.pic_batch_add_run(self._h, C.byref(d), C.byref(rid)))
+        self._nx[rid.value] = int(round(length_lambda * self.cells_per_lambda))
+        return rid.value
+
+    def step(self, n):
+        done = C.c_int64(0)
+        self._check(self._L.pic_batch_step(self._h, n, C.byref(done)))
+        return done.value
+
+    def run_status(self, run):
+        done, fin = C.c_int64(0), C.c_int(0)
+        self._check(self._L.pic_batch_run_status(self._h, run, C.byref(done), C.byref(fin)))
+        return done.value, bool(fin.value)
+
+    def energy(self, run):
+        out = np.zeros(6)
+        self._check(self._L.pic_batch_energy(self._h, run, _dp(out)))
+        return out
+
+    def spectra(self, run, species, nbins, e_min, e_max):
+        counts = np.zeros(nbins)
+        rad = C.c_double(0.0)
+        self._check(self._L.pic_batch_spectra(self._h, run, species, nbins, e_min, e_max, _dp(counts),
+                                              C.byref(rad)))
+        return counts, rad.value
+
+    def particles(self, run, species):
+        n = C.c_int64(0)
+        self._check(self._L.pic_batch_read_particles(self._h, run, species, 0, None, None, None, None, None,
+                                                     C.byref(n)))
+        n = n.value
+        x, px, py, pz = (np.zeros(n) for _ in range(4))
+        flag = np.zeros(n, dtype=np.int32)
+        self._check(self._L.pic_batch_read_particles(self._h, run, species, n, _dp(x), _dp(px), _dp(py), _dp(pz),
+                                                     flag.ctypes.data_as(C.POINTER(C.c_int32)), None))
+        return dict(x=x, px=px, py=py, pz=pz, flag=flag)
+
+    def nx(self, run):
+        return self._nx[run]
+
+    def field(self, run, comp):
+        out = np.zeros(self._nx[run] + 1)
+        n = C.c_int64(0)
+        self._check(self._L.pic_batch_read_fields(self._h, run, comp, len(out), _dp(out), C.byref(n)))
+        return out[: n.value].copy()
+
+    def footprint(self, **desc):
+        d = run_desc(**desc)
+        out = C.c_size_t(0)
+        rc = self._L.pic_batch_run_footprint(self._h, C.byref(d), C.byref(out))
+        if rc != 0:
+            raise PicError(rc, self._L.pic_batch_last_error(None).decode())
+        return out.value
+
+    def release_run(self, run):
+        self._check(self._L.pic_batch_release_run(self._h, run))
+
+    def stats(self):
+        st = Stats()
+        self._check(self._L.pic_batch_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def set_timing(self, on=True):
+        self._check(self._L.pic_batch_set_timing(self._h, int(on)))
+
+
+class Server:
+    """Request loop over a batch (pic_server_*): submit run descriptions, fetch
+    their spectra and energy read-outs when they finish."""
+
+    def __init__(self, cells_per_lambda, max_runs, chunk_steps=64, cfl=0.95, lambda_um=0.8, sort_interval=8,
+                 device=0, hbm_budget_bytes=0):
+        self._L = library()
+        cfg = Config(1.0, cells_per_lambda, cfl, lambda_um, 1, sort_interval, 0, device, 0, hbm_budget_bytes)
+        h = C.c_void_p()
+        rc = self._L.pic_server_create(C.byref(cfg), max_runs, chunk_steps, C.byref(h))
+        if rc != 0:
+            raise PicError(rc, self._L.pic_server_last_error(None).decode())
+        self._h = h
+        self._nbins = {}
+
+    def _err(self, rc):
+        return PicError(rc, self._L.pic_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pic_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, nbins=200, ion_e_max=2000.0, el_e_max=2000.0, **desc):
+        d = run_desc(**desc)
+        t = C.c_int64(0)
+        rc = self._L.pic_server_submit(self._h, C.byref(d), nbins, ion_e_max, el_e_max, C.byref(t))
+        if rc != 0:
+            raise self._err(rc)
+        self._nbins[t.value] = nbins
+        return t.value
+
+    def result(self, ticket, wait_s=0.0):
+        """dict(ion, el, energy, latency_s) when finished, None if not yet."""
+        nb = self._nbins[ticket]
+        ion, el, en = np.zeros(nb), np.zeros(nb), np.zeros(6)
+        lat = C.c_double(0.0)
+        rc = self._L.pic_server_result(self._h, ticket, wait_s, _dp(ion), _dp(el), _dp(en), C.byref(lat))
+        if rc == -5:
+            return None
+        del self._nbins[ticket]
+        if rc != 0:
+            raise self._err(rc)
+        return dict(ion=ion, el=el, energy=en, latency_s=lat.value)
+
+    def stats(self):
+        st = ServerStats()
+        rc = self._L.pic_server_stats(self._h, C.byref(st))
+        if rc != 0:
+            raise self._err(rc)
+        return st.as_dict()

@@ -108,40 +108,7 @@ __global__ void __launch_bounds__(DIAG_T) k_spectrum(DevSpecies sp, int64_t n, d
             if (sh[i]) atomicAdd(&bins[i], static_cast<unsigned long long>(sh[i]));
 }
 
-__global__ void __launch_bounds__(1024) k_rad_flush(double* part, const int32_t* count, double* tally) {
-    __shared__ double sred[32];
-    const int n = count[0];
-    const int t = threadIdx.x;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int i = t;
-    for (; i + 3 * 1024 < n; i += 4 * 1024) {
-        a0 += part[i];
-        a1 += part[i + 1024];
-        a2 += part[i + 2048];
-        a3 += part[i + 3072];
-        part[i] = part[i + 1024] = part[i + 2048] = part[i + 3072] = 0.0;
-    }
-    for (; i < n; i += 1024) {
-        a0 += part[i];
-        part[i] = 0.0;
-    }
-    double v = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((t & 31) == 0) sred[t >> 5] = v;
-    __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int w = 0; w < 32; ++w) s += sred[w];
-        tally[0] += s;
-    }
-}
-
 }  // namespace
-
-void launch_rad_flush(double* rad_part, const int32_t* unit_count, double* tally, cudaStream_t st) {
-    k_rad_flush<<<1, 1024, 0, st>>>(rad_part, unit_count, tally);
-}
 
 int launch_field_energy(const DiagParams& D, double* partials, int max_blocks, cudaStream_t st) {
     int g = (D.Nx + 1 + DIAG_T - 1) / DIAG_T;

@@ -4,7 +4,8 @@
 //   B^{n+1/2} = B^n - (dt/2) curl E^n,
 //   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J^{n+1/2}),
 //   B^{n+1}   = B^{n+1/2} - (dt/2) curl E^{n+1}.
-// Each block owns FIELD_T nodes and recomputes the two guard values it
+// Each block owns FIELD_T nodes of one run (a block table maps blocks to
+// runs) and recomputes the two guard values it
 // needs from its neighbours' old data, so one launch does the whole step
 // (old and new fields live in separate buffers).  The block also converts
 // the fixed-point current to float, zeroes the accumulators of the next
@@ -32,22 +33,31 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
     __shared__ float nEy[T + 2], nEz[T + 2];  // E^{n+1} on nodes [i0-1, i0+T]
     __shared__ float sJy[T + 2], sJz[T + 2];  // J on nodes [i0-1, i0+T]
     const int tid = threadIdx.x;
-    const int i0 = blockIdx.x * T;
-    const int Nx = P.Nx, is = P.is;
-    const float c = P.c, hc = P.hc, fdt = P.fdt, fpi = P.fp_inv, fph = P.fp_inv * 4294967296.0f;
+    const int run = P.blk_run[blockIdx.x];
+    const RunDev& R = P.runs[run];
+    if (!R.active) return;  // block-uniform
+    const int i0 = P.blk_i0[blockIdx.x];
+    const int Nx = R.Nx, is = R.is, glen = R.glen;
+    const int par = static_cast<int>((P.gstep + R.fpar) & 1);
+    const float* const* Fo = R.F[par];
+    float* const* Fn = R.F[1 - par];
+    const unsigned long long* const* Jacc = R.J[par];
+    unsigned long long* const* Jnext = R.J[1 - par];
+    const float* inc = P.inc + 6 * run;
+    const float c = P.c, hc = P.hc, fdt = P.fdt, fpi = R.fp_inv, fph = R.fp_inv * 4294967296.0f;
 
     for (int q = tid; q < T + 4; q += T) {
         const int i = i0 - 2 + q + PADF;  // padded index, >= PADF - 2 >= 0
-        const bool in = i < P.glen;       // the last block reaches past the array end
-        sEy[q] = in ? P.Fo[1][i] : 0.f;
-        sEz[q] = in ? P.Fo[2][i] : 0.f;
+        const bool in = i < glen;       // the last block reaches past the array end
+        sEy[q] = in ? Fo[1][i] : 0.f;
+        sEz[q] = in ? Fo[2][i] : 0.f;
         if (q < T + 3) {
-            sBy[q] = in ? P.Fo[3][i] : 0.f;
-            sBz[q] = in ? P.Fo[4][i] : 0.f;
+            sBy[q] = in ? Fo[3][i] : 0.f;
+            sBz[q] = in ? Fo[4][i] : 0.f;
         }
         if (q >= 1 && q < T + 3) {  // J on nodes [i0-1, i0+T]
-            sJy[q - 1] = in ? fix_to_float(P.Jacc[1][i], fpi, fph) : 0.f;
-            sJz[q - 1] = in ? fix_to_float(P.Jacc[2][i], fpi, fph) : 0.f;
+            sJy[q - 1] = in ? fix_to_float(Jacc[1][i], fpi, fph) : 0.f;
+            sJz[q - 1] = in ? fix_to_float(Jacc[2][i], fpi, fph) : 0.f;
         }
     }
     __syncthreads();
@@ -58,8 +68,8 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         float by = sBy[q] + hc * (sEz[q + 1] - sEz[q]);
         float bz = sBz[q] - hc * (sEy[q + 1] - sEy[q]);
         if (j == is - 1) {  // scattered side of the source plane: remove the incident E at t_n
-            bz += hc * P.inc[0];
-            by -= hc * P.inc[1];
+            bz += hc * inc[0];
+            by -= hc * inc[1];
         }
         hBy[q] = by;
         hBz[q] = bz;
@@ -73,8 +83,8 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         float ey = sEy[q + 1] - c * (hBz[q + 1] - hBz[q]) - fdt * sJy[q];
         float ez = sEz[q + 1] + c * (hBy[q + 1] - hBy[q]) - fdt * sJz[q];
         if (i == is) {  // total side: add the incident B at half node is-1/2, time t_n + dt/2
-            ey += c * P.inc[2];
-            ez += c * P.inc[3];
+            ey += c * inc[2];
+            ez += c * inc[3];
         }
         if (i < 1 || i > Nx - 1) {
             ey = 0.f;
@@ -107,45 +117,45 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         const int q = tid;  // node i: nE[q+1], sE[q+2]; half node i: hB[q+2]
         const int pi = i + PADF;
         if (i <= Nx) {
-            P.Fn[1][pi] = nEy[q + 1];
-            P.Fn[2][pi] = nEz[q + 1];
-            P.Jf[1][pi] = sJy[q + 1];
-            P.Jf[2][pi] = sJz[q + 1];
+            Fn[1][pi] = nEy[q + 1];
+            Fn[2][pi] = nEz[q + 1];
+            R.Jf[1][pi] = sJy[q + 1];
+            R.Jf[2][pi] = sJz[q + 1];
         }
         if (i < Nx) {
             float by = hBy[q + 2] + hc * (nEz[q + 2] - nEz[q + 1]);
             float bz = hBz[q + 2] - hc * (nEy[q + 2] - nEy[q + 1]);
             if (i == is - 1) {  // incident E at t_{n+1}
-                bz += hc * P.inc[4];
-                by -= hc * P.inc[5];
+                bz += hc * inc[4];
+                by -= hc * inc[5];
             }
-            P.Fn[3][pi] = by;
-            P.Fn[4][pi] = bz;
-            const float jx = fix_to_float(P.Jacc[0][pi], fpi, fph);
-            P.Jf[0][pi] = jx;
-            P.Fn[0][pi] = P.Fo[0][pi] - fdt * jx;
+            Fn[3][pi] = by;
+            Fn[4][pi] = bz;
+            const float jx = fix_to_float(Jacc[0][pi], fpi, fph);
+            R.Jf[0][pi] = jx;
+            Fn[0][pi] = Fo[0][pi] - fdt * jx;
         }
         // exact discrete Poynting flux through the accounting planes
         const int a = is + 1, b = Nx - 1;
         if (i == a) {
             const double ey = 0.5 * (static_cast<double>(sEy[q + 2]) + nEy[q + 1]);
             const double ez = 0.5 * (static_cast<double>(sEz[q + 2]) + nEz[q + 1]);
-            P.tally[1] += P.dt * (ey * hBz[q + 1] - ez * hBy[q + 1]);
+            R.tally[1] += P.dt * (ey * hBz[q + 1] - ez * hBy[q + 1]);
         }
         if (i == b) {
             const double ey = 0.5 * (static_cast<double>(sEy[q + 2]) + nEy[q + 1]);
             const double ez = 0.5 * (static_cast<double>(sEz[q + 2]) + nEz[q + 1]);
-            P.tally[2] += P.dt * (ey * hBz[q + 2] - ez * hBy[q + 2]);
+            R.tally[2] += P.dt * (ey * hBz[q + 2] - ez * hBy[q + 2]);
         }
     }
     // zero the accumulators of the next step: owned padded range of this block
     {
-        const int lo = (blockIdx.x == 0) ? 0 : i0 + PADF;
+        const int lo = (i0 == 0) ? 0 : i0 + PADF;
         const int hi = (i0 + T > Nx) ? Nx + 2 * PADF + 1 : i0 + T + PADF;
         for (int pi = lo + tid; pi < hi; pi += T) {
-            P.Jnext[0][pi] = 0ull;
-            P.Jnext[1][pi] = 0ull;
-            P.Jnext[2][pi] = 0ull;
+            Jnext[0][pi] = 0ull;
+            Jnext[1][pi] = 0ull;
+            Jnext[2][pi] = 0ull;
         }
     }
 }

@@ -65,8 +65,11 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
 
     const int u = blockIdx.x;
     if (u >= P.units.count[0]) return;  // block-uniform
+    const RunDev& R = P.runs[P.units.run[u]];
+    if (!R.active) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = P.units.species[u];
+    const int par = static_cast<int>((P.gstep + R.fpar) & 1);
     const int start = P.units.start[u], end = P.units.end[u];
     const int lo = P.units.lo[u], hi = P.units.hi[u];
     const int k = P.k;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const DevSpecies sp = P.sp[s];
+    const DevSpecies sp = R.sp[s][P.cur];
     // the unit's particles are read in 16-byte slots of 4, from the aligned slot
     // before `start` to the aligned slot after `end`; the at most 3 particles
     // of each neighbouring unit in those slots are never written here
@@ -95,14 +98,15 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], P.F[c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
+        for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], R.F[par][c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
     }
 
-    const float qm = P.qm[s], qw = P.qw[s];
+    const float qm = R.qm[s], qw = R.qw[s];
     const float cfl = P.cfl, dt = P.dt, eps = P.eps;
-    const float lscale = P.lscale[s];
-    const int shift = P.lshift[s];
-    const bool rr = P.rr[s] != 0;
+    const float lscale = R.lscale[s];
+    const int shift = R.lshift[s];
+    const bool rr = s == 0 && R.rr != 0;
+    const int Nx = R.Nx;
     const float hq = 0.5f * qm * dt;
     const float jxf = qw / cfl;  // q w dx / dt
     const int nslots = np4 >> 2;
@@ -222,15 +226,15 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
                     }
                 }
                 int cnew = c + d, store_c = cnew;
-                if (cnew < 0) {  // frozen at x = 0
+                if (cnew < 0) {  // frozen at x = 0 (sorts under cell 0)
                     cnew = 0;
                     fn = 0.f;
                     d = 0;
                     store_c = -1;
-                } else if (cnew >= P.Nx) {  // frozen at x = L
-                    cnew = P.Nx;
+                } else if (cnew >= Nx) {  // frozen at x = L (sorts under its last cell Nx-1)
+                    cnew = Nx;
                     fn = 0.f;
-                    store_c = -2;
+                    store_c = -Nx;
                 }
                 // --- deposit records (old bin lb, new bin lb + d)
                 const float ay = 0.5f * qw * vyn, az = 0.5f * qw * vzn;
@@ -316,16 +320,16 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < PUSH_T / 32; ++w) t += sred[w];
-        P.rad_part[u] += t * static_cast<double>(P.rad_w[s]);  // summed into the tally at the next flush
+        P.rad_part[u] += t * static_cast<double>(R.rad_w[s]);  // summed into the tally at the next flush
     }
     // flush the window: node n gets jy_lo of bin n and jy_hi of bin n-1
     for (int i = tid; i < L; i += PUSH_T) {
         const unsigned long long jy = sJ[0][i] + (i > 0 ? sJ[1][i - 1] : 0ull);
         const unsigned long long jz = sJ[2][i] + (i > 0 ? sJ[3][i - 1] : 0ull);
         const unsigned long long jx = sJ[4][i];
-        if (jx) atomicAdd(P.J[0] + p0 + i, jx);
-        if (jy) atomicAdd(P.J[1] + p0 + i, jy);
-        if (jz) atomicAdd(P.J[2] + p0 + i, jz);
+        if (jx) atomicAdd(R.J[par][0] + p0 + i, jx);
+        if (jy) atomicAdd(R.J[par][1] + p0 + i, jy);
+        if (jz) atomicAdd(R.J[par][2] + p0 + i, jz);
     }
 }
 

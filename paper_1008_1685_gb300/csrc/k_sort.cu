@@ -1,22 +1,24 @@
-// Periodic cell sort of the particles and the unit table built from it.
+// Periodic cell sort of the particles of every run of a batch, and the unit
+// table built from it.
 //
-// The sort is a stable counting sort by cell (particles frozen at a wall go
-// last, in their previous order).  It exploits what the push guarantees:
-// a particle moves less than one cell per step, so k steps after the last
-// sort every particle of unit u has a cell in [lo_u - k, hi_u + k].  Hence
-//   1. each unit counts its particles per cell of that window (shared-memory
-//      integer atomics);
-//   2. for each cell the units whose window covers it form a contiguous
-//      range (lo and hi are sorted), found by binary search; the per-cell
-//      totals are scanned into the new cell starts, and every (unit, cell)
-//      pair gets its destination offset in unit order;
+// The sort is a stable counting sort by cell (a particle frozen at a wall
+// sorts under its last cell).  It exploits what the push guarantees: a
+// particle moves less than one cell per step, so k steps after the last sort
+// every particle of unit u has a cell in [lo_u - k, hi_u + k].  Hence, for
+// every active run and species of the batch, in one launch per phase:
+//   1. each unit counts its particles per cell of that window (warp-aggregated
+//      shared-memory integer atomics);
+//   2. for each cell the units whose window covers it form a contiguous range
+//      (lo and hi are sorted within a run and species), found by binary
+//      search; the per-cell totals are scanned into the new cell starts, and
+//      every (unit, cell) pair gets its destination offset in unit order;
 //   3. each unit scatters its particles, ranking equal cells in index order
 //      (warp match + per-warp counts combined in warp order), so the result
 //      does not depend on scheduling;
 //   4. the unit table is rebuilt from the sorted cells: tiles of TILE cells,
 //      split into chunks of at most UNIT_P particles.
-// Every particle is read once and written once; the cell array is read
-// once more for the counts.
+// Every particle is read once and written once; the cell array is read once
+// more for the counts.
 #include <algorithm>
 
 #include "picrr_internal.cuh"
@@ -28,37 +30,33 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SORT_T = 256;
 constexpr int SCAN_T = 1024;
-constexpr int KEY_T = 256;  // keys per block of the per-cell kernels
-constexpr int ESC = SSTR - 1;  // local slot of particles frozen since the last sort
 
-__device__ __forceinline__ int unit_base(const UnitTable& U, int s) { return s == 0 ? 0 : U.count[1]; }
+// sort key of a stored cell: frozen particles (cell = -1 - k) sort under k
+__device__ __forceinline__ int key_of(int c) { return c < 0 ? -1 - c : c; }
 
-// ---- 1. per-unit window counts -------------------------------------------
+// ---- 1. per-unit window counts -------------------------------------------------
 __global__ void __launch_bounds__(SORT_T) k_sort_count(const SortParams S) {
     __shared__ int cnt[SSTR];
     const int u = blockIdx.x;
     if (u >= S.units.count[0]) return;
+    const RunDev& R = S.runs[S.units.run[u]];
+    if (!R.active) return;  // a run that ended keeps its particles where they are
     const int s = S.units.species[u];
     const int start = S.units.start[u], end = S.units.end[u];
     const int wb = S.units.lo[u] - S.k;
     const int L = S.units.hi[u] + S.k + 1 - wb;
     for (int i = threadIdx.x; i < SSTR; i += SORT_T) cnt[i] = 0;
     __syncthreads();
-    const int32_t* cell = S.src[s].cell;
+    const int32_t* cell = R.sp[s][S.cur].cell;
     const int lane = threadIdx.x & 31;
     for (int i0 = start; i0 < end; i0 += SORT_T) {  // block-uniform trip count
         const int i = i0 + threadIdx.x;
         int l = -1;
         if (i < end) {
-            const int c = cell[i];
-            if (c < 0) {
-                l = ESC;
-            } else {
-                l = c - wb;
-                if (!(l >= 0 && l < L && l < ESC)) {
-                    atomicOr(S.meta + 4, ST_WINDOW);
-                    l = -1;
-                }
+            l = key_of(cell[i]) - wb;
+            if (!(l >= 0 && l < L && l < SSTR)) {
+                atomicOr(S.status, ST_WINDOW);
+                l = -1;
             }
         }
         // lanes with the same cell add their count once
@@ -66,23 +64,21 @@ __global__ void __launch_bounds__(SORT_T) k_sort_count(const SortParams S) {
         if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[l], __popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SSTR; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = (i == ESC) ? 0 : cnt[i];
-    if (threadIdx.x == 0) S.esc_cnt[u] = cnt[ESC];
+    for (int i = threadIdx.x; i < SSTR; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = cnt[i];
 }
 
-// Units of species s covering cell key: [u0, u1] (empty if u0 > u1).
-__device__ void covering(const SortParams& S, int s, int key, int& u0, int& u1) {
-    const int b = unit_base(S.units, s), n = S.units.count[1 + s];
-    // first u with hi + k >= key
-    int l = 0, r = n;
+// Units of run `run`, species s whose window covers cell `key`: [u0, u1].
+__device__ void covering(const SortParams& S, int run, int s, int key, int& u0, int& u1) {
+    const int p = 2 * run + s;
+    const int b = S.rs_units[2 * S.nruns + p], n = S.rs_units[p];
+    int l = 0, r = n;  // first u with hi + k >= key
     while (l < r) {
         const int m = (l + r) >> 1;
         if (S.units.hi[b + m] + S.k >= key) r = m; else l = m + 1;
     }
     u0 = b + l;
-    // last u with lo - k <= key
     l = 0;
-    r = n;
+    r = n;  // last u with lo - k <= key
     while (l < r) {
         const int m = (l + r) >> 1;
         if (S.units.lo[b + m] - S.k <= key) l = m + 1; else r = m;
@@ -102,8 +98,8 @@ __device__ __forceinline__ int block_sum_int(int v, int* sh) {
     return t;
 }
 
-// exclusive scan of v over the block (KEY_T threads), plus the block total
-__device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
+// exclusive scan of v over the block (KEY_T threads)
+__device__ __forceinline__ int block_excl_scan(int v, int* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = v;
 #pragma unroll
@@ -123,42 +119,11 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
         if (lane < KEY_T / 32) sh[lane] = w;
     }
     __syncthreads();
-    const int r = x - v + (warp > 0 ? sh[warp - 1] : 0);
-    *total = sh[KEY_T / 32 - 1];
-    return r;
+    return x - v + (warp > 0 ? sh[warp - 1] : 0);
 }
 
-// ---- 2a. per-cell totals (and per-block sums of them) -------------------------
-__global__ void __launch_bounds__(KEY_T) k_sort_totals(const SortParams S) {
-    __shared__ int sh[KEY_T / 32];
-    const int s = blockIdx.y;
-    const int key = blockIdx.x * KEY_T + threadIdx.x;
-    int tot = 0;
-    if (key < S.Nx) {
-        int u0, u1;
-        covering(S, s, key, u0, u1);
-        for (int u = u0; u <= u1; ++u) {
-            const int l = key - (S.units.lo[u] - S.k);
-            if (l >= 0 && l < ESC) tot += S.cnt[static_cast<size_t>(u) * SSTR + l];
-        }
-        S.keycount[s][key] = tot;
-    }
-    const int b = block_sum_int(tot, sh);
-    if (threadIdx.x == 0) S.blocksum[s][blockIdx.x] = b;
-}
-
-// per-block sums of key counts filled by atomics (fresh load)
-__global__ void __launch_bounds__(KEY_T) k_block_sums(const SortParams S) {
-    __shared__ int sh[KEY_T / 32];
-    const int s = blockIdx.y;
-    const int key = blockIdx.x * KEY_T + threadIdx.x;
-    const int v = key < S.Nx ? S.keycount[s][key] : 0;
-    const int b = block_sum_int(v, sh);
-    if (threadIdx.x == 0) S.blocksum[s][blockIdx.x] = b;
-}
-
-// exclusive scan of n ints held contiguously, by one block of SCAN_T threads
-// (each thread a contiguous range); writes out[0..n) and returns the total
+// exclusive scan of n ints by one block of SCAN_T threads (each thread a
+// contiguous range); writes out[0..n) and returns the total
 __device__ int block_scan_ranges(const int32_t* in, int32_t* out, int n, int* sh) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n + SCAN_T - 1) / SCAN_T;
@@ -195,49 +160,56 @@ __device__ int block_scan_ranges(const int32_t* in, int32_t* out, int n, int* sh
     return total;
 }
 
-// ---- 2b. scan of the per-block key sums; escape offsets of the units ----------
-// One block per species.  blockstart[s][b] = keys before block b; keystart[s][Nx]
-// = active particles; esc_off[u] = destination of unit u's first escaped
-// particle (after all active ones); meta[2+s] = escapes since the last sort.
-__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const SortParams S, int nkb, int with_units) {
-    __shared__ int sh[SCAN_T / 32];
-    const int s = blockIdx.x;
-    const int act = block_scan_ranges(S.blocksum[s], S.blockstart[s], nkb, sh);
-    if (threadIdx.x == 0) S.keystart[s][S.Nx] = act;
-    if (!with_units) return;
-    const int ub = unit_base(S.units, s), nu = S.units.count[1 + s];
-    const int esc = block_scan_ranges(S.esc_cnt + ub, S.esc_off + ub, nu, sh);
-    for (int u = threadIdx.x; u < nu; u += SCAN_T) S.esc_off[ub + u] += act;
-    if (threadIdx.x == 0) S.meta[2 + s] = esc;
-}
-
-// keystart[s][key] from the block starts and a block scan of the key counts
-__global__ void __launch_bounds__(KEY_T) k_keystart(const SortParams S) {
+// ---- 2a. per-cell totals (and per-block sums of them) --------------------------
+// grid (key blocks of the largest run, runs, species)
+__global__ void __launch_bounds__(KEY_T) k_sort_totals(const SortParams S) {
     __shared__ int sh[KEY_T / 32];
-    const int s = blockIdx.y;
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active || blockIdx.x * KEY_T >= R.Nx) return;  // block-uniform
     const int key = blockIdx.x * KEY_T + threadIdx.x;
-    const int v = key < S.Nx ? S.keycount[s][key] : 0;
-    int total;
-    const int r = block_excl_scan(v, sh, &total);
-    if (key < S.Nx) S.keystart[s][key] = S.blockstart[s][blockIdx.x] + r;
+    int tot = 0;
+    if (key < R.Nx) {
+        int u0, u1;
+        covering(S, blockIdx.y, s, key, u0, u1);
+        for (int u = u0; u <= u1; ++u) {
+            const int l = key - (S.units.lo[u] - S.k);
+            if (l >= 0 && l < SSTR) tot += S.cnt[static_cast<size_t>(u) * SSTR + l];
+        }
+        R.keycount[s][key] = tot;
+    }
+    const int b = block_sum_int(tot, sh);
+    if (threadIdx.x == 0) R.blocksum[s][blockIdx.x] = b;
 }
 
-// ---- 2c. cell starts and the destination of every (unit, cell) pair ----------
+// ---- 2b. scan of the per-block sums, one block per (run, species) --------------
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const SortParams S) {
+    __shared__ int sh[SCAN_T / 32];
+    const RunDev& R = S.runs[blockIdx.x];
+    const int s = blockIdx.y;
+    if (!R.active) return;
+    const int nkb = (R.Nx + KEY_T - 1) / KEY_T;
+    const int total = block_scan_ranges(R.blocksum[s], R.blockstart[s], nkb, sh);
+    if (threadIdx.x == 0) R.keystart[s][R.Nx] = total;
+}
+
+// ---- 2c. cell starts and the destination of every (unit, cell) pair -------------
 __global__ void __launch_bounds__(KEY_T) k_sort_offsets(const SortParams S) {
     __shared__ int sh[KEY_T / 32];
-    const int s = blockIdx.y;
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active || blockIdx.x * KEY_T >= R.Nx) return;
     const int key = blockIdx.x * KEY_T + threadIdx.x;
-    const int v = key < S.Nx ? S.keycount[s][key] : 0;
-    int total;
-    const int r = block_excl_scan(v, sh, &total);
-    if (key >= S.Nx) return;
-    int run = S.blockstart[s][blockIdx.x] + r;
-    S.keystart[s][key] = run;
+    const int v = key < R.Nx ? R.keycount[s][key] : 0;
+    const int r = block_excl_scan(v, sh);
+    if (key >= R.Nx) return;
+    int run = R.blockstart[s][blockIdx.x] + r;
+    R.keystart[s][key] = run;
     int u0, u1;
-    covering(S, s, key, u0, u1);
+    covering(S, blockIdx.y, s, key, u0, u1);
     for (int u = u0; u <= u1; ++u) {
         const int l = key - (S.units.lo[u] - S.k);
-        if (l >= 0 && l < ESC) {
+        if (l >= 0 && l < SSTR) {
             const size_t q = static_cast<size_t>(u) * SSTR + l;
             S.offs[q] = run;
             run += S.cnt[q];
@@ -245,7 +217,7 @@ __global__ void __launch_bounds__(KEY_T) k_sort_offsets(const SortParams S) {
     }
 }
 
-__device__ __forceinline__ void copy_particle(const DevSpecies& a, DevSpecies& b, int i, int d) {
+__device__ __forceinline__ void copy_particle(const DevSpecies& a, const DevSpecies& b, int i, int d) {
     b.cell[d] = a.cell[i];
     b.off[d] = a.off[i];
     b.px[d] = a.px[i];
@@ -254,30 +226,20 @@ __device__ __forceinline__ void copy_particle(const DevSpecies& a, DevSpecies& b
     b.id[d] = a.id[i];
 }
 
-// ---- 3. stable scatter ------------------------------------------------------
+// ---- 3. stable scatter ----------------------------------------------------------
 __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
     __shared__ int base[SSTR];
     __shared__ int wcnt[SORT_T / 32][SSTR];
     const int u = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (u >= S.max_units) {
-        // particles frozen before the last sort keep their order at the very end
-        for (int s = 0; s < 2; ++s) {
-            const int old_act = S.meta[s];
-            const int dst0 = S.keystart[s][S.Nx] + S.meta[2 + s];
-            DevSpecies dst = S.dst[s];
-            for (int i = old_act + (u - S.max_units) * SORT_T + tid; i < S.n[s];
-                 i += (gridDim.x - S.max_units) * SORT_T)
-                copy_particle(S.src[s], dst, i, dst0 + (i - old_act));
-        }
-        return;
-    }
     if (u >= S.units.count[0]) return;
+    const RunDev& R = S.runs[S.units.run[u]];
+    if (!R.active) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = S.units.species[u];
     const int start = S.units.start[u], end = S.units.end[u];
     const int wb = S.units.lo[u] - S.k;
-    const DevSpecies src = S.src[s];
-    DevSpecies dst = S.dst[s];
+    const DevSpecies src = R.sp[s][S.cur];
+    const DevSpecies dst = R.sp[s][1 - S.cur];
     for (int i = tid; i < SSTR; i += SORT_T) base[i] = 0;
     for (int i = tid; i < (SORT_T / 32) * SSTR; i += SORT_T) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -286,12 +248,8 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
         const int i = c0 + tid;
         int key = -1;
         if (i < end) {
-            const int c = src.cell[i];
-            if (c < 0) key = ESC;
-            else {
-                const int l = c - wb;
-                key = (l >= 0 && l < ESC) ? l : -1;  // out of window cannot happen (counted as error)
-            }
+            const int l = key_of(src.cell[i]) - wb;
+            key = (l >= 0 && l < SSTR) ? l : -1;  // out of window cannot happen (counted as an error)
         }
         const unsigned peers = __match_any_sync(FULL, key);
         const int rw = __popc(peers & lt);
@@ -302,7 +260,7 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
         if (key >= 0) {
             int r = base[key] + rw;
             for (int w = 0; w < warp; ++w) r += wcnt[w][key];
-            dest = (key == ESC) ? S.esc_off[u] + r : S.offs[static_cast<size_t>(u) * SSTR + key] + r;
+            dest = S.offs[static_cast<size_t>(u) * SSTR + key] + r;
         }
         __syncthreads();
         if (leader && key >= 0) {
@@ -314,98 +272,184 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
     }
 }
 
-// ---- 4. unit table from sorted cells ------------------------------------------
-// 4a. units per tile (TILE cells, at most UNIT_P particles a unit), scanned
-// per species by one block: tile_first[s][t] = first unit of tile t.
+// ---- 4. unit table from sorted cells -------------------------------------------
+// 4a. units per tile of one (run, species), scanned: tile_first[t] = first
+// unit of tile t within the pair; rs_units[2 r + s] = the pair's units.
 __global__ void __launch_bounds__(SCAN_T) k_tile_units(const SortParams S) {
     __shared__ int sh[SCAN_T / 32];
-    const int ntiles = (S.Nx + TILE - 1) / TILE;
-    int base = 0;
-    for (int s = 0; s < 2; ++s) {
-        const int32_t* ks = S.keystart[s];
-        for (int t = threadIdx.x; t < ntiles; t += SCAN_T) {
-            const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, S.Nx)];
-            S.tile_n[s][t] = (te - ts + UNIT_P - 1) / UNIT_P;
-        }
-        __syncthreads();
-        const int nu = block_scan_ranges(S.tile_n[s], S.tile_first[s], ntiles, sh);
-        if (threadIdx.x == 0) {
-            S.tile_first[s][ntiles] = nu;
-            S.units.count[1 + s] = nu;
-            S.meta[s] = ks[S.Nx];  // active particles at this sort
-        }
-        base += nu;
-        __syncthreads();
+    const int r = blockIdx.x, s = blockIdx.y;
+    const RunDev& R = S.runs[r];
+    if (!R.active || R.n[s] == 0) {
+        if (threadIdx.x == 0) S.rs_units[2 * r + s] = 0;
+        return;
     }
-    if (threadIdx.x == 0) S.units.count[0] = min(base, S.max_units);
+    const int ntiles = (R.Nx + TILE - 1) / TILE;
+    const int32_t* ks = R.keystart[s];
+    for (int t = threadIdx.x; t < ntiles; t += SCAN_T) {
+        const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
+        R.tile_n[s][t] = (te - ts + UNIT_P - 1) / UNIT_P;
+    }
+    __syncthreads();
+    const int nu = block_scan_ranges(R.tile_n[s], R.tile_first[s], ntiles, sh);
+    if (threadIdx.x == 0) {
+        R.tile_first[s][ntiles] = nu;
+        S.rs_units[2 * r + s] = nu;
+    }
 }
 
-// 4b. one thread per unit
-__global__ void k_fill_units(const SortParams S) {
+// 4b. unit bases of every (run, species) pair, in run-major order
+__global__ void __launch_bounds__(SCAN_T) k_unit_bases(const SortParams S) {
+    __shared__ int sh[SCAN_T / 32];
+    const int np = 2 * S.nruns;
+    const int total = block_scan_ranges(S.rs_units, S.rs_units + np, np, sh);
+    if (threadIdx.x == 0) S.units.count[0] = min(total, S.max_units);
+}
+
+// 4c. one thread per unit; the sorted particles are in buffer `ubuf`
+__global__ void k_fill_units(const SortParams S, int ubuf) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= S.units.count[0]) return;
-    const int n0 = S.units.count[1];
-    const int s = u < n0 ? 0 : 1;
-    const int v = u - (s ? n0 : 0);
-    const int ntiles = (S.Nx + TILE - 1) / TILE;
-    const int32_t* tf = S.tile_first[s];
-    int l = 0, r = ntiles;  // last tile t with tf[t] <= v
+    const int np = 2 * S.nruns;
+    const int32_t* first = S.rs_units + np;  // exclusive scan of the pair counts
+    int l = 0, r = np;  // last pair with first[p] <= u and a unit count > 0
     while (r - l > 1) {
         const int m = (l + r) >> 1;
-        if (tf[m] <= v) l = m; else r = m;
+        if (first[m] <= u) l = m; else r = m;
     }
-    const int t = l;
-    const int32_t* ks = S.keystart[s];
-    const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, S.Nx)];
+    while (S.rs_units[l] == 0 && l > 0) --l;  // skip empty pairs sharing the same start
+    const int run = l >> 1, s = l & 1;
+    const RunDev& R = S.runs[run];
+    const int v = u - first[l];
+    const int ntiles = (R.Nx + TILE - 1) / TILE;
+    const int32_t* tf = R.tile_first[s];
+    int a0 = 0, b0 = ntiles;  // last tile t with tf[t] <= v
+    while (b0 - a0 > 1) {
+        const int m = (a0 + b0) >> 1;
+        if (tf[m] <= v) a0 = m; else b0 = m;
+    }
+    const int t = a0;
+    const int32_t* ks = R.keystart[s];
+    const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
     const int a = ts + (v - tf[t]) * UNIT_P;
     const int b = min(a + UNIT_P, te);
+    const int32_t* cell = R.sp[s][ubuf].cell;
+    S.units.run[u] = run;
     S.units.species[u] = s;
     S.units.start[u] = a;
     S.units.end[u] = b;
-    S.units.lo[u] = S.dst[s].cell[a];
-    S.units.hi[u] = S.dst[s].cell[b - 1];
+    S.units.lo[u] = key_of(cell[a]);
+    S.units.hi[u] = key_of(cell[b - 1]);
 }
 
-// ---- histogram of sorted, freshly loaded particles ---------------------------
-// warp-aggregated: lanes holding the same cell add their count once
+// ---- histogram of already sorted particles (fresh load) -------------------------
+// grid (blocks, runs, species); warp-aggregated
 __global__ void k_hist(const SortParams S) {
-    const int s = blockIdx.y;
-    const int64_t n = S.n[s];
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active) return;
+    const int n = R.n[s];
     const int lane = threadIdx.x & 31;
-    for (int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); b < n;
-         b += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t i = b + lane;
-        const int c = i < n ? S.dst[s].cell[i] : -1;
+    const int32_t* cell = R.sp[s][S.cur].cell;
+    for (int b = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += gridDim.x * blockDim.x) {
+        const int i = b + lane;
+        const int c = i < n ? key_of(cell[i]) : -1;
         const unsigned peers = __match_any_sync(FULL, c);
-        if (c >= 0 && c < S.Nx && lane == __ffs(peers) - 1) atomicAdd(&S.keycount[s][c], __popc(peers));
+        if (c >= 0 && c < R.Nx && lane == __ffs(peers) - 1) atomicAdd(&R.keycount[s][c], __popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(KEY_T) k_block_sums(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active || blockIdx.x * KEY_T >= R.Nx) return;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    const int v = key < R.Nx ? R.keycount[s][key] : 0;
+    const int b = block_sum_int(v, sh);
+    if (threadIdx.x == 0) R.blocksum[s][blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(KEY_T) k_keystart(const SortParams S) {
+    __shared__ int sh[KEY_T / 32];
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active || blockIdx.x * KEY_T >= R.Nx) return;
+    const int key = blockIdx.x * KEY_T + threadIdx.x;
+    const int v = key < R.Nx ? R.keycount[s][key] : 0;
+    const int r = block_excl_scan(v, sh);
+    if (key < R.Nx) R.keystart[s][key] = R.blockstart[s][blockIdx.x] + r;
+}
+
+__global__ void k_zero_keycount(const SortParams S) {
+    const RunDev& R = S.runs[blockIdx.y];
+    const int s = blockIdx.z;
+    if (!R.active) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R.Nx + 2; i += gridDim.x * blockDim.x)
+        R.keycount[s][i] = 0;
+}
+
+// ---- radiated energy per run: sum of its electron units, fixed order ------------
+__global__ void __launch_bounds__(1024) k_rad_flush(const RunDev* runs, const int32_t* rs_units, double* part) {
+    __shared__ double sred[32];
+    const RunDev& R = runs[blockIdx.x];
+    if (!R.active) return;
+    const int b = rs_units[2 * gridDim.x + 2 * blockIdx.x], n = rs_units[2 * blockIdx.x];  // electron units
+    const int t = threadIdx.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = t;
+    for (; i + 3 * 1024 < n; i += 4 * 1024) {
+        a0 += part[b + i];
+        a1 += part[b + i + 1024];
+        a2 += part[b + i + 2048];
+        a3 += part[b + i + 3072];
+        part[b + i] = part[b + i + 1024] = part[b + i + 2048] = part[b + i + 3072] = 0.0;
+    }
+    for (; i < n; i += 1024) {
+        a0 += part[b + i];
+        part[b + i] = 0.0;
+    }
+    double v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((t & 31) == 0) sred[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 32; ++w) s += sred[w];
+        R.tally[0] += s;
     }
 }
 
 }  // namespace
 
-void launch_sort(const SortParams& S, int n_unit_blocks, cudaStream_t st, int* launches) {
-    const int kb = (S.Nx + KEY_T - 1) / KEY_T;
-    k_sort_count<<<n_unit_blocks, SORT_T, 0, st>>>(S);
-    k_sort_totals<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
-    k_scan_blocks<<<2, SCAN_T, 0, st>>>(S, kb, 1);
-    k_sort_offsets<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
-    k_sort_scatter<<<n_unit_blocks + 64, SORT_T, 0, st>>>(S);
-    k_tile_units<<<1, SCAN_T, 0, st>>>(S);
-    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S);
-    *launches += 7;
+void launch_sort(const SortParams& S, cudaStream_t st, int* launches) {
+    const dim3 kg(S.kb_max, S.nruns, 2);
+    k_sort_count<<<S.max_units, SORT_T, 0, st>>>(S);
+    k_sort_totals<<<kg, KEY_T, 0, st>>>(S);
+    k_scan_blocks<<<dim3(S.nruns, 2), SCAN_T, 0, st>>>(S);
+    k_sort_offsets<<<kg, KEY_T, 0, st>>>(S);
+    k_sort_scatter<<<S.max_units, SORT_T, 0, st>>>(S);
+    k_tile_units<<<dim3(S.nruns, 2), SCAN_T, 0, st>>>(S);
+    k_unit_bases<<<1, SCAN_T, 0, st>>>(S);
+    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S, 1 - S.cur);
+    *launches += 8;
 }
 
-void launch_build_units_from_sorted(const SortParams& S, cudaStream_t st, int* launches) {
-    const int kb = (S.Nx + KEY_T - 1) / KEY_T;
-    cudaMemsetAsync(S.keycount[0], 0, sizeof(int32_t) * (S.Nx + 2), st);
-    cudaMemsetAsync(S.keycount[1], 0, sizeof(int32_t) * (S.Nx + 2), st);
-    k_hist<<<dim3(256, 2), 256, 0, st>>>(S);
-    k_block_sums<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
-    k_scan_blocks<<<2, SCAN_T, 0, st>>>(S, kb, 0);
-    k_keystart<<<dim3(kb, 2), KEY_T, 0, st>>>(S);
-    k_tile_units<<<1, SCAN_T, 0, st>>>(S);
-    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S);
-    *launches += 6;
+void launch_build_units(const SortParams& S, cudaStream_t st, int* launches) {
+    const dim3 kg(S.kb_max, S.nruns, 2);
+    k_zero_keycount<<<dim3(64, S.nruns, 2), 256, 0, st>>>(S);
+    k_hist<<<dim3(256, S.nruns, 2), 256, 0, st>>>(S);
+    k_block_sums<<<kg, KEY_T, 0, st>>>(S);
+    k_scan_blocks<<<dim3(S.nruns, 2), SCAN_T, 0, st>>>(S);
+    k_keystart<<<kg, KEY_T, 0, st>>>(S);
+    k_tile_units<<<dim3(S.nruns, 2), SCAN_T, 0, st>>>(S);
+    k_unit_bases<<<1, SCAN_T, 0, st>>>(S);
+    k_fill_units<<<(S.max_units + 255) / 256, 256, 0, st>>>(S, S.cur);
+    *launches += 8;
+}
+
+void launch_rad_flush(const RunDev* runs, int nruns, const int32_t* rs_units, double* rad_part, cudaStream_t st) {
+    k_rad_flush<<<nruns, 1024, 0, st>>>(runs, rs_units, rad_part);
 }
 
 // ---- foil loader -------------------------------------------------------------

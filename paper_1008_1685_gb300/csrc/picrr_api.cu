@@ -1,11 +1,18 @@
-// Host side of the picrr C ABI: argument checks, device memory, the step
-// loop (push kernel, Yee kernel, periodic sort), read-backs and counters.
-// See include/picrr.h for the contract of every entry point.
+// Host side of the picrr C ABI.
+//
+// Everything runs on a Batch: R independent runs (each its own grid, foil,
+// laser, particle arrays) stepped together, one launch per kernel per step
+// for all active runs.  A pic_sim handle is a batch of one run; a pic_batch
+// handle exposes the batch itself.  The host side does argument checks,
+// device memory (stream-ordered allocation charged to a budget), the device
+// run table, the laser source values of each step (double precision), the
+// step loop (push kernel, Yee kernel, periodic sort), read-backs and
+// counters.  See include/picrr.h for the contract of every entry point.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <numeric>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
@@ -13,82 +20,19 @@
 #include "picrr.h"
 #include "picrr_internal.cuh"
 
-using namespace picrr;
+namespace picrr {
 
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kReUm = 2.8179403262e-9;    // classical electron radius, um (CODATA 2018)
-constexpr double kMec2MeV = 0.51099895000;   // electron rest energy, MeV
-constexpr double kMpMe = 1836.15267343;      // proton mass / electron mass
-constexpr double kMuMe = 1822.888486209;     // atomic mass unit / electron mass
+constexpr double kReUm = 2.8179403262e-9;   // classical electron radius, um (CODATA 2018)
+constexpr double kMec2MeV = 0.51099895000;  // electron rest energy, MeV
+constexpr double kMpMe = 1836.15267343;     // proton mass / electron mass
+constexpr double kMuMe = 1822.888486209;    // atomic mass unit / electron mass
 constexpr int kMaxDiagBlocks = 1024;
+constexpr int kIncRing = 64;                // slots of the per-step laser-source upload ring
 
-thread_local std::string g_create_error;  // failures of calls without a handle
-
-struct HostSpecies {
-    int64_t n = 0;
-    bool loaded = false;
-    DevSpecies buf[2] = {};
-    int cur = 0;
-    double w = 0.0, q = 0.0, m = 1.0;
-};
-
-struct EventPair {
-    cudaEvent_t a, b;
-    int kind;  // 0 push, 1 field, 2 sort
-};
-
-}  // namespace
-
-namespace picrr {
-void set_null_handle_error(const std::string& msg) { g_create_error = msg; }
-}  // namespace picrr
-
-struct pic_sim {
-    pic_config cfg{};
-    int Nx = 0, is = 8, sort_interval = 8, device = 0;
-    double dx = 0, dt = 0, cfl = 0, eps = 0;
-    cudaStream_t stream = nullptr, own_stream = nullptr;
-    size_t bytes = 0, budget = 0;
-    std::vector<std::pair<void*, size_t>> allocs;
-
-    size_t glen = 0;
-    float* F[2][5] = {};
-    int fcur = 0;
-    unsigned long long* Jacc[2][3] = {};
-    float* Jf[3] = {};
-    double* tally = nullptr;  // [4]
-    int* status = nullptr;
-    double* diag_partials = nullptr;
-    double* diag_out = nullptr;  // [8]
-    unsigned long long* bins = nullptr;
-    int bins_cap = 0;
-
-    HostSpecies sp[2];
-    int max_units = 0;
-    UnitTable units{};
-    double* rad_part = nullptr;
-    int32_t *cnt = nullptr, *offs = nullptr, *esc_cnt = nullptr, *esc_off = nullptr;
-    int32_t *keycount[2] = {}, *keystart[2] = {}, *meta = nullptr;
-    int32_t *blocksum[2] = {}, *blockstart[2] = {}, *tile_n[2] = {}, *tile_first[2] = {};
-
-    int64_t step = 0;
-    int since_sort = 0;
-    bool prepared = false, laser_set = false, fields_set = false;
-    LaserParams laser{};
-    int fp_bits = 40;
-
-    int64_t launches = 0, push_launches = 0, sorts = 0, timed_push = 0;
-    bool timing = false;
-    double push_ms = 0, field_ms = 0, sort_ms = 0;
-    std::vector<EventPair> pending;
-    std::vector<cudaEvent_t> ev_free;
-
-    std::string err;
-};
-
-namespace {
+thread_local std::string g_null_error;  // failures of calls without a handle
 
 struct DeviceGuard {
     int prev = -1;
@@ -101,277 +45,25 @@ struct DeviceGuard {
     }
 };
 
-pic_status fail(pic_sim* s, pic_status st, const std::string& msg) {
-    if (s) s->err = msg;
-    else g_create_error = msg;
-    return st;
-}
-
-pic_status cuda_fail(pic_sim* s, cudaError_t e, const char* where) {
-    return fail(s, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-#define PIC_CK(s, call)                                         \
-    do {                                                        \
-        cudaError_t e_ = (call);                                \
-        if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
-    } while (0)
-
-// Allocate zeroed device memory charged to the handle's budget.  Appends to
-// `fresh` so a failing call can release what it took.
-pic_status dalloc(pic_sim* s, void** out, size_t bytes, std::vector<void*>* fresh) {
-    *out = nullptr;
-    if (bytes == 0) bytes = 16;
-    bytes = (bytes + 255) & ~static_cast<size_t>(255);
-    if (s->budget && s->bytes + bytes > s->budget)
-        return fail(s, PIC_ERR_OOM, "device memory budget exceeded (" + std::to_string(s->bytes + bytes) +
-                                        " > " + std::to_string(s->budget) + " bytes)");
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(s, PIC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    }
-    e = cudaMemsetAsync(p, 0, bytes, s->stream);
-    if (e != cudaSuccess) {
-        cudaFree(p);
-        return cuda_fail(s, e, "cudaMemsetAsync");
-    }
-    s->allocs.emplace_back(p, bytes);
-    s->bytes += bytes;
-    if (fresh) fresh->push_back(p);
-    *out = p;
-    return PIC_OK;
-}
-
-void dfree(pic_sim* s, void* p) {
-    if (!p) return;
-    for (size_t i = 0; i < s->allocs.size(); ++i) {
-        if (s->allocs[i].first == p) {
-            s->bytes -= s->allocs[i].second;
-            s->allocs.erase(s->allocs.begin() + static_cast<long>(i));
-            break;
-        }
-    }
-    cudaFree(p);
-}
-
-void release(pic_sim* s, std::vector<void*>& fresh) {
-    cudaStreamSynchronize(s->stream);
-    for (void* p : fresh) dfree(s, p);
-    fresh.clear();
-}
-
-template <class T>
-pic_status dalloc_t(pic_sim* s, T** out, size_t count, std::vector<void*>* fresh) {
-    void* p = nullptr;
-    pic_status st = dalloc(s, &p, count * sizeof(T), fresh);
-    *out = static_cast<T*>(p);
-    return st;
-}
-
-pic_status alloc_species(pic_sim* s, HostSpecies& h, int64_t n, std::vector<void*>& fresh) {
-    const size_t cap = static_cast<size_t>((n + 3) / 4 * 4 + 8);
-    for (int b = 0; b < 2; ++b) {
-        DevSpecies& d = h.buf[b];
-        pic_status st;
-        if ((st = dalloc_t(s, &d.cell, cap, &fresh)) != PIC_OK) return st;
-        if ((st = dalloc_t(s, &d.off, cap, &fresh)) != PIC_OK) return st;
-        if ((st = dalloc_t(s, &d.px, cap, &fresh)) != PIC_OK) return st;
-        if ((st = dalloc_t(s, &d.py, cap, &fresh)) != PIC_OK) return st;
-        if ((st = dalloc_t(s, &d.pz, cap, &fresh)) != PIC_OK) return st;
-        if ((st = dalloc_t(s, &d.id, cap, &fresh)) != PIC_OK) return st;
-    }
-    h.n = n;
-    h.cur = 0;
-    return PIC_OK;
-}
-
-bool before_first_step(pic_sim* s) { return s->step == 0 && !s->prepared; }
-
-cudaEvent_t take_event(pic_sim* s) {
-    if (!s->ev_free.empty()) {
-        cudaEvent_t e = s->ev_free.back();
-        s->ev_free.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// Record an event pair around a launch sequence when timing is on.
-struct Timed {
-    pic_sim* s;
-    EventPair ep{};
-    bool on;
-    Timed(pic_sim* sim, int kind) : s(sim), on(sim->timing) {
-        if (on) {
-            ep.a = take_event(s);
-            ep.b = take_event(s);
-            ep.kind = kind;
-            cudaEventRecord(ep.a, s->stream);
-        }
-    }
-    ~Timed() {
-        if (on) {
-            cudaEventRecord(ep.b, s->stream);
-            s->pending.push_back(ep);
-        }
-    }
+struct HostSpecies {
+    int64_t n = 0;
+    bool loaded = false;
+    double w = 0.0, q = 0.0, m = 1.0;
 };
 
-void collect_timing(pic_sim* s) {
-    for (EventPair& ep : s->pending) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ep.a, ep.b) == cudaSuccess) {
-            if (ep.kind == 0) {
-                s->push_ms += ms;
-                s->timed_push++;
-            } else if (ep.kind == 1) {
-                s->field_ms += ms;
-            } else {
-                s->sort_ms += ms;
-            }
-        }
-        s->ev_free.push_back(ep.a);
-        s->ev_free.push_back(ep.b);
-    }
-    s->pending.clear();
-}
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;  // 0 push, 1 field, 2 sort
+};
 
-SortParams sort_params(pic_sim* s) {
-    SortParams S{};
-    for (int k = 0; k < 2; ++k) {
-        S.src[k] = s->sp[k].buf[s->sp[k].cur];
-        S.dst[k] = s->sp[k].buf[1 - s->sp[k].cur];
-        S.n[k] = s->sp[k].loaded ? s->sp[k].n : 0;
-        S.keycount[k] = s->keycount[k];
-        S.keystart[k] = s->keystart[k];
-        S.blocksum[k] = s->blocksum[k];
-        S.blockstart[k] = s->blockstart[k];
-        S.tile_n[k] = s->tile_n[k];
-        S.tile_first[k] = s->tile_first[k];
-    }
-    S.units = s->units;
-    S.cnt = s->cnt;
-    S.offs = s->offs;
-    S.esc_cnt = s->esc_cnt;
-    S.esc_off = s->esc_off;
-    S.meta = s->meta;
-    S.Nx = s->Nx;
-    S.k = s->since_sort;
-    S.max_units = s->max_units;
-    return S;
-}
+}  // namespace
 
-// Allocate the unit table and sort scratch, fix the fixed-point scale and
-// build the first unit table (particles are loaded in cell order).
-pic_status prepare(pic_sim* s) {
-    std::vector<void*> fresh;
-    const int ntiles = (s->Nx + TILE - 1) / TILE;
-    int64_t mu = 1;
-    double bound = 0.0;
-    for (int k = 0; k < 2; ++k) {
-        if (!s->sp[k].loaded) continue;
-        mu += (s->sp[k].n + UNIT_P - 1) / UNIT_P + ntiles + 1;
-        bound += static_cast<double>(s->sp[k].n) * std::fabs(s->sp[k].q * s->sp[k].w) / s->cfl;
-    }
-    if (mu > (1 << 30)) return fail(s, PIC_ERR_INVALID_ARG, "too many work units");
-    s->max_units = static_cast<int>(mu);
-    // fixed point: every partial sum of the current is bounded by `bound`;
-    // keep bound * 2^fp below 2^61.
-    int fp = 40;
-    if (bound > 0.0) fp = static_cast<int>(std::floor(61.0 - std::log2(bound)));
-    s->fp_bits = std::max(8, std::min(52, fp));
-    pic_status st;
-    const size_t mu_z = static_cast<size_t>(mu);
-    if ((st = dalloc_t(s, &s->units.species, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->units.start, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->units.end, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->units.lo, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->units.hi, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->units.count, 4, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->rad_part, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->cnt, mu_z * SSTR, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->offs, mu_z * SSTR, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->esc_cnt, mu_z, &fresh)) != PIC_OK) goto bad;
-    if ((st = dalloc_t(s, &s->esc_off, mu_z, &fresh)) != PIC_OK) goto bad;
-    for (int k = 0; k < 2; ++k) {
-        if ((st = dalloc_t(s, &s->keycount[k], static_cast<size_t>(s->Nx) + 2, &fresh)) != PIC_OK) goto bad;
-        if ((st = dalloc_t(s, &s->keystart[k], static_cast<size_t>(s->Nx) + 2, &fresh)) != PIC_OK) goto bad;
-        const size_t nkb = static_cast<size_t>(s->Nx) / 256 + 2, ntl = static_cast<size_t>(s->Nx) / TILE + 3;
-        if ((st = dalloc_t(s, &s->blocksum[k], nkb, &fresh)) != PIC_OK) goto bad;
-        if ((st = dalloc_t(s, &s->blockstart[k], nkb, &fresh)) != PIC_OK) goto bad;
-        if ((st = dalloc_t(s, &s->tile_n[k], ntl, &fresh)) != PIC_OK) goto bad;
-        if ((st = dalloc_t(s, &s->tile_first[k], ntl, &fresh)) != PIC_OK) goto bad;
-    }
-    if ((st = dalloc_t(s, &s->meta, 8, &fresh)) != PIC_OK) goto bad;
-    {
-        // the loaded particles sit in buffer `cur` in cell order: build units from it
-        SortParams S = sort_params(s);
-        for (int k = 0; k < 2; ++k) S.dst[k] = s->sp[k].buf[s->sp[k].cur];
-        int nl = 0;
-        launch_build_units_from_sorted(S, s->stream, &nl);
-        s->launches += nl;
-        cudaError_t e = cudaStreamSynchronize(s->stream);
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            st = cuda_fail(s, e, "build units");
-            goto bad;
-        }
-    }
-    s->prepared = true;
-    return PIC_OK;
-bad:
-    release(s, fresh);
-    s->units = UnitTable{};
-    s->rad_part = nullptr;
-    s->cnt = s->offs = s->esc_cnt = s->esc_off = s->meta = nullptr;
-    s->keycount[0] = s->keycount[1] = s->keystart[0] = s->keystart[1] = nullptr;
-    for (int k = 0; k < 2; ++k) s->blocksum[k] = s->blockstart[k] = s->tile_n[k] = s->tile_first[k] = nullptr;
-    return st;
-}
-
-PushParams push_params(pic_sim* s) {
-    PushParams P{};
-    for (int k = 0; k < 2; ++k) {
-        const HostSpecies& h = s->sp[k];
-        P.sp[k] = h.buf[h.cur];
-        P.qm[k] = static_cast<float>(h.q / h.m);
-        P.qw[k] = static_cast<float>(h.q * h.w);
-        P.rad_w[k] = static_cast<float>(h.w * s->dx * h.m);
-        P.rr[k] = (k == PIC_ELECTRON && s->cfg.rr_on) ? 1 : 0;
-    }
-    for (int c = 0; c < 5; ++c) P.F[c] = s->F[s->fcur][c];
-    for (int c = 0; c < 3; ++c) P.J[c] = s->Jacc[s->step & 1][c];
-    P.units = s->units;
-    P.rad_part = s->rad_part;
-    P.status = s->status;
-    P.Nx = s->Nx;
-    P.k = s->since_sort;
-    P.cfl = static_cast<float>(s->cfl);
-    P.dt = static_cast<float>(s->dt);
-    P.eps = static_cast<float>(s->eps);
-    for (int k = 0; k < 2; ++k) {
-        // a warp record sums at most 16 particles of one lane (a thread holds at
-        // most UNIT_P / PUSH_T + 4 particles of a unit) over 32 lanes, each value
-        // bounded by |q w| max(1, 1/cfl): keep every lane below 2^26
-        static_assert(UNIT_P / PUSH_T + 4 <= 16, "running record bound");
-        const double vmax = std::fabs(s->sp[k].q * s->sp[k].w) * std::max(1.0, 1.0 / s->cfl);
-        int ls = 40;
-        if (vmax > 0.0) ls = static_cast<int>(std::floor(26.0 - std::log2(16.0 * vmax)));
-        ls = std::min(ls, s->fp_bits);
-        P.lscale[k] = std::ldexp(1.0f, ls);
-        P.lshift[k] = s->fp_bits - ls;
-    }
-    return P;
-}
+void set_null_handle_error(const std::string& msg) { g_null_error = msg; }
 
 // Incident field of the laser at retarded time t (double precision phase and
 // envelope): Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az.  LP: ay = a0 g sin t;
 // CP: a0/sqrt2 per component, ay = a g sin t, az = -a g cos t.
-void incident(const LaserParams& L, double t, float* ay, float* az) {
+static void incident(const LaserParams& L, double t, float* ay, float* az) {
     *ay = 0.f;
     *az = 0.f;
     if (!L.on || t < 0.0 || t > L.tau) return;
@@ -397,54 +89,225 @@ void incident(const LaserParams& L, double t, float* ay, float* az) {
     }
 }
 
-FieldParams field_params(pic_sim* s) {
-    FieldParams Q{};
-    for (int c = 0; c < 5; ++c) {
-        Q.Fo[c] = s->F[s->fcur][c];
-        Q.Fn[c] = s->F[1 - s->fcur][c];
-    }
-    for (int c = 0; c < 3; ++c) {
-        Q.Jacc[c] = s->Jacc[s->step & 1][c];
-        Q.Jnext[c] = s->Jacc[(s->step + 1) & 1][c];
-        Q.Jf[c] = s->Jf[c];
-    }
-    Q.tally = s->tally;
-    Q.Nx = s->Nx;
-    Q.is = s->is;
-    Q.glen = static_cast<int>(s->glen);
-    Q.n = s->step;
-    Q.dt = s->dt;
-    Q.dx = s->dx;
-    Q.c = static_cast<float>(s->cfl);
-    Q.hc = static_cast<float>(0.5 * s->cfl);
-    Q.fdt = static_cast<float>(s->dt);
-    Q.fp_inv = std::ldexp(1.0f, -s->fp_bits);
-    const double tn = static_cast<double>(s->step) * s->dt;
-    const double ts[3] = {tn, tn + 0.5 * s->dt + 0.5 * s->dx, tn + s->dt};
-    for (int k = 0; k < 3; ++k) incident(s->laser, ts[k], &Q.inc[2 * k], &Q.inc[2 * k + 1]);
-    return Q;
+// One run of a batch, host side.
+struct RunHost {
+    bool used = false;      // slot holds a run
+    bool active = false;    // stepped by the batch
+    bool started = false;   // took part in at least one step (setup frozen)
+    bool finished = false;  // reached its step count
+    double length_lambda = 0.0;
+    int Nx = 0, is = 8, rr = 1;
+    uint64_t seed = 1;
+    HostSpecies sp[2];
+    LaserParams laser{};
+    bool laser_set = false, fields_set = false;
+    int64_t admit_step = 0;    // batch step of its first step
+    int64_t steps_target = 0;  // 0: unlimited
+    int64_t steps_done = 0;
+    int pbuf = 0, fbuf = 0;    // particle / field buffer of a finished run
+    int fp_bits = 40;
+    size_t glen = 0;
+    std::vector<std::pair<void*, size_t>> mem;  // device allocations of this run
+    RunDev dev{};                               // mirror of the device table entry
+};
+
+struct Batch {
+    pic_config cfg{};
+    int device = 0, sort_interval = 8, max_runs = 1;
+    double dx = 0, dt = 0, cfl = 0, eps = 0;
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    size_t bytes = 0, budget = 0;
+    std::vector<std::pair<void*, size_t>> mem;  // batch-level allocations
+
+    std::vector<RunHost> runs;
+    RunDev* d_runs = nullptr;
+    RunDev* h_runs = nullptr;  // pinned staging of the run table
+    int32_t* d_blk_run = nullptr;
+    int32_t* d_blk_i0 = nullptr;
+    int nblk = 0, blk_cap = 0;
+    float* d_inc = nullptr;
+    float* h_inc = nullptr;  // pinned ring [kIncRing][max_runs * 6]
+    cudaEvent_t inc_ev[kIncRing] = {};
+    int inc_slot = 0;
+
+    UnitTable units{};
+    int max_units = 0;
+    double* rad_part = nullptr;
+    int32_t *cnt = nullptr, *offs = nullptr, *rs_units = nullptr;
+    int* d_status = nullptr;
+    double* diag_partials = nullptr;
+    double* diag_out = nullptr;
+    unsigned long long* bins = nullptr;
+    int bins_cap = 0;
+
+    int64_t gstep = 0;
+    int since_sort = 0;
+    int cur = 0;
+    bool table_dirty = true, layout_dirty = true;
+
+    int64_t launches = 0, push_launches = 0, sorts = 0, timed_push = 0;
+    bool timing = false;
+    double push_ms = 0, field_ms = 0, sort_ms = 0;
+    std::vector<EventPair> pending;
+    std::vector<cudaEvent_t> ev_free;
+
+    std::string err;
+};
+
+namespace {
+
+pic_status fail(Batch* b, pic_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_null_error = msg;
+    return st;
 }
 
-}  // namespace
+pic_status cuda_fail(Batch* b, cudaError_t e, const char* where) {
+    cudaGetLastError();
+    return fail(b, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
 
-// ============================================================================
-extern "C" {
+#define PIC_CK(b, call)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((b), e_, #call); \
+    } while (0)
 
-pic_status pic_create(const pic_config* cfg, pic_sim** out) {
-    if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out is NULL");
+// Stream-ordered, zeroed device allocation charged to the batch's budget.
+pic_status dalloc(Batch* b, std::vector<std::pair<void*, size_t>>& owner, void** out, size_t bytes) {
     *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~static_cast<size_t>(255);
+    if (b->budget && b->bytes + bytes > b->budget)
+        return fail(b, PIC_ERR_OOM, "device memory budget exceeded (" + std::to_string(b->bytes + bytes) + " > " +
+                                        std::to_string(b->budget) + " bytes)");
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(b, PIC_ERR_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(p, 0, bytes, b->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(p, b->stream);
+        return cuda_fail(b, e, "cudaMemsetAsync");
+    }
+    owner.emplace_back(p, bytes);
+    b->bytes += bytes;
+    *out = p;
+    return PIC_OK;
+}
+
+template <class T>
+pic_status dalloc_t(Batch* b, std::vector<std::pair<void*, size_t>>& owner, T** out, size_t count) {
+    void* p = nullptr;
+    pic_status st = dalloc(b, owner, &p, count * sizeof(T));
+    *out = static_cast<T*>(p);
+    return st;
+}
+
+void free_all(Batch* b, std::vector<std::pair<void*, size_t>>& owner) {
+    for (auto& a : owner) {
+        cudaFreeAsync(a.first, b->stream);
+        b->bytes -= a.second;
+    }
+    owner.clear();
+}
+
+// Free allocations made after index `mark` of `owner` (undo of a failed call).
+void free_from(Batch* b, std::vector<std::pair<void*, size_t>>& owner, size_t mark) {
+    while (owner.size() > mark) {
+        cudaFreeAsync(owner.back().first, b->stream);
+        b->bytes -= owner.back().second;
+        owner.pop_back();
+    }
+}
+
+// Free one batch-level allocation.
+void free_one(Batch* b, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < b->mem.size(); ++i)
+        if (b->mem[i].first == p) {
+            cudaFreeAsync(p, b->stream);
+            b->bytes -= b->mem[i].second;
+            b->mem.erase(b->mem.begin() + static_cast<long>(i));
+            return;
+        }
+}
+
+cudaEvent_t take_event(Batch* b) {
+    if (!b->ev_free.empty()) {
+        cudaEvent_t e = b->ev_free.back();
+        b->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Timed {
+    Batch* b;
+    EventPair ep{};
+    bool on;
+    Timed(Batch* bb, int kind) : b(bb), on(bb->timing) {
+        if (on) {
+            ep.a = take_event(b);
+            ep.b = take_event(b);
+            ep.kind = kind;
+            cudaEventRecord(ep.a, b->stream);
+        }
+    }
+    ~Timed() {
+        if (on) {
+            cudaEventRecord(ep.b, b->stream);
+            b->pending.push_back(ep);
+        }
+    }
+};
+
+void collect_timing(Batch* b) {
+    for (EventPair& ep : b->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ep.a, ep.b) == cudaSuccess) {
+            if (ep.kind == 0) {
+                b->push_ms += ms;
+                b->timed_push++;
+            } else if (ep.kind == 1) {
+                b->field_ms += ms;
+            } else {
+                b->sort_ms += ms;
+            }
+        }
+        b->ev_free.push_back(ep.a);
+        b->ev_free.push_back(ep.b);
+    }
+    b->pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// batch life cycle
+// ---------------------------------------------------------------------------
+
+pic_status validate_common(const pic_config* cfg) {
     if (!cfg) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfg is NULL");
-    if (!(cfg->length_lambda > 0.0) || !(cfg->cells_per_lambda > 0.0))
-        return fail(nullptr, PIC_ERR_INVALID_ARG, "length_lambda and cells_per_lambda must be > 0");
+    if (!(cfg->cells_per_lambda > 0.0) || !std::isfinite(cfg->cells_per_lambda))
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "cells_per_lambda must be > 0");
     if (!(cfg->cfl > 0.0 && cfg->cfl < 1.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfl must be in (0, 1)");
     if (!(cfg->lambda_um > 0.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "lambda_um must be > 0");
     if (cfg->sort_interval < 0 || cfg->sort_interval > KMAX)
         return fail(nullptr, PIC_ERR_INVALID_ARG, "sort_interval must be in [0, 32]");
-    const double ncell = cfg->length_lambda * cfg->cells_per_lambda;
-    if (!(ncell >= 16.0 && ncell <= 1.0e9)) return fail(nullptr, PIC_ERR_INVALID_ARG, "Nx must be in [16, 1e9]");
-    const int Nx = static_cast<int>(std::llround(ncell));
-    const int is = cfg->source_node ? cfg->source_node : 8;
-    if (is < 2 || is > Nx - 4) return fail(nullptr, PIC_ERR_INVALID_ARG, "source_node must be in [2, Nx-4]");
+    return PIC_OK;
+}
+
+void batch_destroy(Batch* b);
+
+pic_status batch_create(const pic_config* cfg, int max_runs, Batch** out) {
+    *out = nullptr;
+    pic_status st = validate_common(cfg);
+    if (st != PIC_OK) return st;
+    if (max_runs < 1 || max_runs > (1 << 16))
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "max_runs must be in [1, 65536]");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -452,89 +315,211 @@ pic_status pic_create(const pic_config* cfg, pic_sim** out) {
     }
     if (cfg->device < 0 || cfg->device >= ndev) return fail(nullptr, PIC_ERR_INVALID_ARG, "device out of range");
     DeviceGuard g(cfg->device);
-
-    pic_sim* s = new pic_sim();
-    s->cfg = *cfg;
-    s->device = cfg->device;
-    s->Nx = Nx;
-    s->is = is;
-    s->sort_interval = cfg->sort_interval ? cfg->sort_interval : 8;
-    s->dx = 2.0 * kPi / cfg->cells_per_lambda;
-    s->cfl = cfg->cfl;
-    s->dt = cfg->cfl * s->dx;
-    s->eps = (4.0 / 3.0) * kPi * kReUm / cfg->lambda_um;
-    s->budget = cfg->hbm_budget_bytes;
-    if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    Batch* b = new Batch();
+    b->cfg = *cfg;
+    b->device = cfg->device;
+    b->max_runs = max_runs;
+    b->sort_interval = cfg->sort_interval ? cfg->sort_interval : 8;
+    b->dx = 2.0 * kPi / cfg->cells_per_lambda;
+    b->cfl = cfg->cfl;
+    b->dt = cfg->cfl * b->dx;
+    b->eps = (4.0 / 3.0) * kPi * kReUm / cfg->lambda_um;
+    b->budget = cfg->hbm_budget_bytes;
+    b->runs.resize(static_cast<size_t>(max_runs));
+    if (cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        delete s;
+        delete b;
         return fail(nullptr, PIC_ERR_CUDA, "cudaStreamCreate failed");
     }
-    s->stream = s->own_stream;
-    s->glen = (static_cast<size_t>(Nx) + 1 + 2 * PADF + 4 + 3) / 4 * 4;
-    pic_status st = PIC_OK;
-    for (int b = 0; b < 2 && st == PIC_OK; ++b)
-        for (int c = 0; c < 5 && st == PIC_OK; ++c) st = dalloc_t(s, &s->F[b][c], s->glen, nullptr);
-    for (int b = 0; b < 2 && st == PIC_OK; ++b)
-        for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(s, &s->Jacc[b][c], s->glen, nullptr);
-    for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(s, &s->Jf[c], s->glen, nullptr);
-    if (st == PIC_OK) st = dalloc_t(s, &s->tally, 4, nullptr);
-    if (st == PIC_OK) st = dalloc_t(s, &s->status, 4, nullptr);
-    if (st == PIC_OK) st = dalloc_t(s, &s->diag_partials, kMaxDiagBlocks, nullptr);
-    if (st == PIC_OK) st = dalloc_t(s, &s->diag_out, 8, nullptr);
-    if (st == PIC_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = PIC_ERR_CUDA;
-    if (st != PIC_OK) {
-        g_create_error = s->err;
-        pic_destroy(s);
+    b->stream = b->own_stream;
+    if ((st = dalloc_t(b, b->mem, &b->d_runs, static_cast<size_t>(max_runs))) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->d_inc, static_cast<size_t>(max_runs) * 6)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->d_status, 4)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->diag_partials, kMaxDiagBlocks)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->diag_out, 8)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->rs_units, static_cast<size_t>(4) * max_runs)) != PIC_OK) {
+        g_null_error = b->err;
+        batch_destroy(b);
         return st;
     }
-    *out = s;
-    return PIC_OK;
-}
-
-pic_status pic_set_stream(pic_sim* s, void* stream) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    DeviceGuard g(s->device);
-    cudaStreamSynchronize(s->stream);
-    s->stream = stream ? static_cast<cudaStream_t>(stream) : s->own_stream;
-    return PIC_OK;
-}
-
-pic_status pic_load_foil(pic_sim* s, double x0_lambda, double thickness_lambda, double ne_over_nc, int ion_Z,
-                         double ion_A, int ppc) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "load_foil after the first step");
-    if (s->sp[0].loaded || s->sp[1].loaded) return fail(s, PIC_ERR_STATE, "particles already loaded");
-    if (!(ne_over_nc > 0.0) || ion_Z < 1 || !(ion_A > 0.0) || ppc < 1)
-        return fail(s, PIC_ERR_INVALID_ARG, "need ne > 0, Z >= 1, A > 0, ppc >= 1");
-    const double cpl = s->cfg.cells_per_lambda;
-    const long long c0 = std::llround(x0_lambda * cpl), nc = std::llround(thickness_lambda * cpl);
-    if (!(std::isfinite(x0_lambda) && std::isfinite(thickness_lambda)) || c0 < 0 || nc < 1 || c0 + nc > s->Nx)
-        return fail(s, PIC_ERR_INVALID_ARG, "foil must lie inside the box and span at least one cell");
-    const long long n = nc * static_cast<long long>(ppc);
-    if (n > 2147483647LL - 64) return fail(s, PIC_ERR_INVALID_ARG, "more than 2^31 particles per species");
-    DeviceGuard g(s->device);
-    std::vector<void*> fresh;
-    pic_status st;
-    for (int k = 0; k < 2; ++k)
-        if ((st = alloc_species(s, s->sp[k], n, fresh)) != PIC_OK) {
-            release(s, fresh);
-            s->sp[0] = HostSpecies{};
-            s->sp[1] = HostSpecies{};
-            return st;
-        }
-    launch_foil(s->sp[0].buf[0], s->sp[1].buf[0], static_cast<int>(c0), static_cast<int>(nc), ppc, s->cfg.seed,
-                s->stream);
-    s->launches++;
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        release(s, fresh);
-        s->sp[0] = HostSpecies{};
-        s->sp[1] = HostSpecies{};
-        return cuda_fail(s, e, "foil loader");
+    if (cudaMallocHost(&b->h_runs, sizeof(RunDev) * max_runs) != cudaSuccess ||
+        cudaMallocHost(&b->h_inc, sizeof(float) * 6 * max_runs * kIncRing) != cudaSuccess) {
+        cudaGetLastError();
+        batch_destroy(b);
+        return fail(nullptr, PIC_ERR_OOM, "pinned host allocation failed");
     }
-    HostSpecies& el = s->sp[0];
-    HostSpecies& io = s->sp[1];
+    std::memset(b->h_runs, 0, sizeof(RunDev) * max_runs);
+    for (int i = 0; i < kIncRing; ++i) cudaEventCreateWithFlags(&b->inc_ev[i], cudaEventDisableTiming);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        batch_destroy(b);
+        return cuda_fail(nullptr, e, "create");
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+void batch_destroy(Batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (EventPair& ep : b->pending) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    for (cudaEvent_t e : b->ev_free) cudaEventDestroy(e);
+    for (auto& r : b->runs) free_all(b, r.mem);
+    free_all(b, b->mem);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < kIncRing; ++i)
+        if (b->inc_ev[i]) cudaEventDestroy(b->inc_ev[i]);
+    if (b->h_runs) cudaFreeHost(b->h_runs);
+    if (b->h_inc) cudaFreeHost(b->h_inc);
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    delete b;
+}
+
+// New run slot with its grid arrays allocated (no particles yet).
+pic_status run_open(Batch* b, double length_lambda, int source_node, int rr_on, uint64_t seed, int* out_id) {
+    const double ncell = length_lambda * b->cfg.cells_per_lambda;
+    if (!(length_lambda > 0.0) || !(ncell >= 16.0 && ncell <= 1.0e9))
+        return fail(b, PIC_ERR_INVALID_ARG, "length_lambda * cells_per_lambda must be in [16, 1e9]");
+    const int Nx = static_cast<int>(std::llround(ncell));
+    const int is = source_node ? source_node : 8;
+    if (is < 2 || is > Nx - 4) return fail(b, PIC_ERR_INVALID_ARG, "source_node must be in [2, Nx-4]");
+    int id = -1;
+    for (int i = 0; i < b->max_runs; ++i)
+        if (!b->runs[i].used) {
+            id = i;
+            break;
+        }
+    if (id < 0) return fail(b, PIC_ERR_STATE, "no free run slot (max_runs reached)");
+    RunHost& r = b->runs[id];
+    r = RunHost();
+    r.length_lambda = length_lambda;
+    r.Nx = Nx;
+    r.is = is;
+    r.rr = rr_on ? 1 : 0;
+    r.seed = seed;
+    r.glen = (static_cast<size_t>(Nx) + 1 + 2 * PADF + 4 + 3) / 4 * 4;
+    RunDev& d = r.dev;
+    d.Nx = Nx;
+    d.is = is;
+    d.glen = static_cast<int>(r.glen);
+    d.rr = r.rr;
+    pic_status st = PIC_OK;
+    for (int x = 0; x < 2 && st == PIC_OK; ++x)
+        for (int c = 0; c < 5 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.F[x][c], r.glen);
+    for (int x = 0; x < 2 && st == PIC_OK; ++x)
+        for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.J[x][c], r.glen);
+    for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.Jf[c], r.glen);
+    if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.tally, 4);
+    const size_t nk = static_cast<size_t>(Nx) + 2, nkb = static_cast<size_t>(Nx) / KEY_T + 2,
+                 ntl = static_cast<size_t>(Nx) / TILE + 3;
+    for (int s = 0; s < 2 && st == PIC_OK; ++s) {
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.keycount[s], nk);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.keystart[s], nk);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.blocksum[s], nkb);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.blockstart[s], nkb);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.tile_n[s], ntl);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.tile_first[s], ntl);
+    }
+    if (st != PIC_OK) {
+        free_all(b, r.mem);
+        r = RunHost();
+        return st;
+    }
+    r.used = true;
+    *out_id = id;
+    return PIC_OK;
+}
+
+size_t rounded(size_t bytes) { return ((bytes ? bytes : 16) + 255) & ~static_cast<size_t>(255); }
+
+// Device bytes a run of length_lambda with n particles per species takes in a
+// batch: its grid, sort scratch and particle buffers as run_open and
+// alloc_species allocate them, plus its share of the batch's unit table and
+// Yee block table with the unit table's growth factor (1.5).
+size_t run_footprint(const Batch* b, double length_lambda, int64_t n) {
+    const int64_t Nx = std::llround(length_lambda * b->cfg.cells_per_lambda);
+    const size_t glen = (static_cast<size_t>(Nx) + 1 + 2 * PADF + 4 + 3) / 4 * 4;
+    size_t t = 10 * rounded(glen * 4) + 6 * rounded(glen * 8) + 3 * rounded(glen * 4) + rounded(32);
+    const size_t nk = static_cast<size_t>(Nx) + 2, nkb = static_cast<size_t>(Nx) / KEY_T + 2,
+                 ntl = static_cast<size_t>(Nx) / TILE + 3;
+    t += 2 * (2 * rounded(nk * 4) + 2 * rounded(nkb * 4) + 2 * rounded(ntl * 4));
+    const size_t cap = static_cast<size_t>((n + 3) / 4 * 4 + 8);
+    t += 2 * 2 * 6 * rounded(cap * 4);
+    const int64_t ntiles = (Nx + TILE - 1) / TILE;
+    const size_t units = static_cast<size_t>(2 * ((n + UNIT_P - 1) / UNIT_P + ntiles + 1));
+    t += units * (6 * 4 + 8 + 2 * SSTR * 4) * 3 / 2;
+    t += static_cast<size_t>(Nx / FIELD_T + 1) * 8 * 3 / 2;
+    return t;
+}
+
+void run_release(Batch* b, int id) {
+    RunHost& r = b->runs[id];
+    if (!r.used) return;
+    if (r.active) b->layout_dirty = true;
+    b->table_dirty = true;
+    free_all(b, r.mem);
+    r = RunHost();
+}
+
+pic_status alloc_species(Batch* b, RunHost& r, int s, int64_t n) {
+    const size_t cap = static_cast<size_t>((n + 3) / 4 * 4 + 8);
+    pic_status st = PIC_OK;
+    for (int x = 0; x < 2 && st == PIC_OK; ++x) {
+        DevSpecies& d = r.dev.sp[s][x];
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.cell, cap);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.off, cap);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.px, cap);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.py, cap);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.pz, cap);
+        if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.id, cap);
+    }
+    if (st == PIC_OK) {
+        r.sp[s].n = n;
+        r.dev.n[s] = static_cast<int32_t>(n);
+    }
+    return st;
+}
+
+void clear_species(RunHost& r, int s) {
+    r.sp[s] = HostSpecies();
+    r.dev.n[s] = 0;
+    for (int x = 0; x < 2; ++x) r.dev.sp[s][x] = DevSpecies{};
+}
+
+pic_status run_load_foil(Batch* b, int id, double x0_lambda, double thickness_lambda, double ne_over_nc, int ion_Z,
+                         double ion_A, int ppc) {
+    RunHost& r = b->runs[id];
+    if (r.started) return fail(b, PIC_ERR_STATE, "load_foil after the first step");
+    if (r.sp[0].loaded || r.sp[1].loaded) return fail(b, PIC_ERR_STATE, "particles already loaded");
+    if (!(ne_over_nc > 0.0) || !std::isfinite(ne_over_nc) || ion_Z < 1 || !(ion_A > 0.0) || ppc < 1)
+        return fail(b, PIC_ERR_INVALID_ARG, "need ne > 0, Z >= 1, A > 0, ppc >= 1");
+    const double cpl = b->cfg.cells_per_lambda;
+    if (!(std::isfinite(x0_lambda) && std::isfinite(thickness_lambda)))
+        return fail(b, PIC_ERR_INVALID_ARG, "foil position and thickness must be finite");
+    const long long c0 = std::llround(x0_lambda * cpl), nc = std::llround(thickness_lambda * cpl);
+    if (c0 < 0 || nc < 1 || c0 + nc > r.Nx)
+        return fail(b, PIC_ERR_INVALID_ARG, "foil must lie inside the box and span at least one cell");
+    const long long n = nc * static_cast<long long>(ppc);
+    if (n > 2147483647LL - 64) return fail(b, PIC_ERR_INVALID_ARG, "more than 2^31 particles per species");
+    const size_t mark = r.mem.size();
+    pic_status st = alloc_species(b, r, 0, n);
+    if (st == PIC_OK) st = alloc_species(b, r, 1, n);
+    if (st != PIC_OK) {
+        free_from(b, r.mem, mark);
+        clear_species(r, 0);
+        clear_species(r, 1);
+        return st;
+    }
+    // loaded particles go to the buffer the batch's kernels read at their first step
+    launch_foil(r.dev.sp[0][b->cur], r.dev.sp[1][b->cur], static_cast<int>(c0), static_cast<int>(nc), ppc, r.seed,
+                b->stream);
+    b->launches++;
+    HostSpecies& el = r.sp[0];
+    HostSpecies& io = r.sp[1];
     el.q = -1.0;
     el.m = 1.0;
     el.w = ne_over_nc / ppc;
@@ -545,267 +530,505 @@ pic_status pic_load_foil(pic_sim* s, double x0_lambda, double thickness_lambda, 
     return PIC_OK;
 }
 
-pic_status pic_load_particles(pic_sim* s, int species, int64_t n, const int32_t* cell, const double* off,
-                              const double* px, const double* py, const double* pz, double weight, double charge,
+// Upload host particle arrays (already in cell order) into the load buffer.
+pic_status run_upload(Batch* b, RunHost& r, int s, int64_t n, const int32_t* cell, const float* off, const float* px,
+                      const float* py, const float* pz, const int32_t* id, double w, double q, double m) {
+    const size_t mark = r.mem.size();
+    pic_status st = alloc_species(b, r, s, n);
+    if (st != PIC_OK) {
+        free_from(b, r.mem, mark);
+        clear_species(r, s);
+        return st;
+    }
+    const DevSpecies& d = r.dev.sp[s][b->cur];
+    const size_t b4 = static_cast<size_t>(n) * 4;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(d.cell, cell, b4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.off, off, b4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.px, px, b4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.py, py, b4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d.pz, pz, b4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) {
+            if (id) {
+                e = cudaMemcpyAsync(d.id, id, b4, cudaMemcpyHostToDevice, b->stream);
+            } else {
+                launch_iota(d.id, n, b->stream);
+                b->launches++;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host arrays may be released after return
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        free_from(b, r.mem, mark);
+        clear_species(r, s);
+        return cuda_fail(b, e, "upload particles");
+    }
+    r.sp[s].w = w;
+    r.sp[s].q = q;
+    r.sp[s].m = m;
+    r.sp[s].loaded = true;
+    return PIC_OK;
+}
+
+pic_status check_species_args(Batch* b, RunHost& r, int species, int64_t n, double weight, double charge,
                               double mass) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (species != PIC_ELECTRON && species != PIC_ION) return fail(s, PIC_ERR_INVALID_ARG, "bad species");
-    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "load_particles after the first step");
-    if (s->sp[species].loaded) return fail(s, PIC_ERR_STATE, "species already loaded");
-    if (n < 0 || n > 2147483647LL - 64) return fail(s, PIC_ERR_INVALID_ARG, "n must be in [0, 2^31 - 64]");
-    if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(s, PIC_ERR_INVALID_ARG, "NULL array");
+    if (species != PIC_ELECTRON && species != PIC_ION) return fail(b, PIC_ERR_INVALID_ARG, "bad species");
+    if (r.started) return fail(b, PIC_ERR_STATE, "load_particles after the first step");
+    if (r.sp[species].loaded) return fail(b, PIC_ERR_STATE, "species already loaded");
+    if (n < 0 || n > 2147483647LL - 64) return fail(b, PIC_ERR_INVALID_ARG, "n must be in [0, 2^31 - 64]");
     if (!(mass > 0.0) || !std::isfinite(weight) || !std::isfinite(charge))
-        return fail(s, PIC_ERR_INVALID_ARG, "mass must be > 0, weight and charge finite");
+        return fail(b, PIC_ERR_INVALID_ARG, "mass must be > 0, weight and charge finite");
+    return PIC_OK;
+}
+
+pic_status run_load_particles_f32(Batch* b, int id, int species, int64_t n, const int32_t* cell, const float* off,
+                                  const float* px, const float* py, const float* pz, double weight, double charge,
+                                  double mass) {
+    RunHost& r = b->runs[id];
+    pic_status st = check_species_args(b, r, species, n, weight, charge, mass);
+    if (st != PIC_OK) return st;
+    if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(b, PIC_ERR_INVALID_ARG, "NULL array");
+    bool sorted = true;
+    for (int64_t i = 0; i < n; ++i) {
+        if (cell[i] < 0 || cell[i] >= r.Nx) return fail(b, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
+        if (!(off[i] >= 0.0f && off[i] < 1.0f)) return fail(b, PIC_ERR_INVALID_ARG, "offset out of [0, 1)");
+        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]))
+            return fail(b, PIC_ERR_INVALID_ARG, "non-finite momentum");
+        if (i > 0 && cell[i] < cell[i - 1]) sorted = false;
+    }
+    if (sorted) return run_upload(b, r, species, n, cell, off, px, py, pz, nullptr, weight, charge, mass);
+    // units need cell order: stable sort; ids keep the load order
+    std::vector<int64_t> order(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i) order[static_cast<size_t>(i)] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return cell[a] < cell[c]; });
     std::vector<int32_t> hc(static_cast<size_t>(n)), hid(static_cast<size_t>(n));
     std::vector<float> ho(static_cast<size_t>(n)), hx(static_cast<size_t>(n)), hy(static_cast<size_t>(n)),
         hz(static_cast<size_t>(n));
-    std::vector<int64_t> order(static_cast<size_t>(n));
-    for (int64_t i = 0; i < n; ++i) {
-        if (cell[i] < 0 || cell[i] >= s->Nx) return fail(s, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
-        const float o = static_cast<float>(off[i]);
-        if (!(o >= 0.0f && o < 1.0f)) return fail(s, PIC_ERR_INVALID_ARG, "offset out of [0, 1) in float");
-        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]))
-            return fail(s, PIC_ERR_INVALID_ARG, "non-finite momentum");
-        order[static_cast<size_t>(i)] = i;
-    }
-    // the unit table needs particles in cell order: stable sort, ids keep the load order
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cell[a] < cell[b]; });
     for (int64_t j = 0; j < n; ++j) {
         const int64_t i = order[static_cast<size_t>(j)];
         hc[j] = cell[i];
-        ho[j] = static_cast<float>(off[i]);
-        hx[j] = static_cast<float>(px[i]);
-        hy[j] = static_cast<float>(py[i]);
-        hz[j] = static_cast<float>(pz[i]);
+        ho[j] = off[i];
+        hx[j] = px[i];
+        hy[j] = py[i];
+        hz[j] = pz[i];
         hid[j] = static_cast<int32_t>(i);
     }
-    DeviceGuard g(s->device);
-    std::vector<void*> fresh;
-    HostSpecies h;
-    pic_status st = alloc_species(s, h, n, fresh);
-    if (st != PIC_OK) {
-        release(s, fresh);
-        return st;
-    }
-    const DevSpecies& d = h.buf[0];
-    const size_t b4 = static_cast<size_t>(n) * 4;
-    cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        e = cudaMemcpyAsync(d.cell, hc.data(), b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.off, ho.data(), b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.px, hx.data(), b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.py, hy.data(), b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.pz, hz.data(), b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.id, hid.data(), b4, cudaMemcpyHostToDevice, s->stream);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) {
-        release(s, fresh);
-        return cuda_fail(s, e, "upload particles");
-    }
-    h.w = weight;
-    h.q = charge;
-    h.m = mass;
-    h.loaded = true;
-    s->sp[species] = h;
+    return run_upload(b, r, species, n, hc.data(), ho.data(), hx.data(), hy.data(), hz.data(), hid.data(), weight,
+                      charge, mass);
+}
+
+pic_status run_inject_laser(Batch* b, int id, double a0, int polarization, int envelope, double duration_periods,
+                            double rise_periods) {
+    RunHost& r = b->runs[id];
+    if (r.started) return fail(b, PIC_ERR_STATE, "inject_laser after the first step");
+    if (r.laser_set) return fail(b, PIC_ERR_STATE, "laser already set");
+    if (!(a0 >= 0.0 && std::isfinite(a0))) return fail(b, PIC_ERR_INVALID_ARG, "a0 must be finite and >= 0");
+    if (polarization != PIC_LP && polarization != PIC_CP) return fail(b, PIC_ERR_INVALID_ARG, "bad polarization");
+    if (envelope != PIC_ENV_SIN2 && envelope != PIC_ENV_TRAPEZOID)
+        return fail(b, PIC_ERR_INVALID_ARG, "bad envelope");
+    if (!(duration_periods > 0.0 && std::isfinite(duration_periods)))
+        return fail(b, PIC_ERR_INVALID_ARG, "duration must be > 0");
+    if (envelope == PIC_ENV_TRAPEZOID && !(rise_periods > 0.0 && 2.0 * rise_periods <= duration_periods))
+        return fail(b, PIC_ERR_INVALID_ARG, "trapezoid needs 0 < 2 rise <= duration");
+    r.laser.on = 1;
+    r.laser.pol = polarization;
+    r.laser.env = envelope;
+    r.laser.a0 = a0;
+    r.laser.tau = duration_periods * 2.0 * kPi;
+    r.laser.rise = rise_periods * 2.0 * kPi;
+    r.laser_set = true;
     return PIC_OK;
 }
 
-pic_status pic_load_particles_f32(pic_sim* s, int species, int64_t n, const int32_t* cell, const float* off,
-                                  const float* px, const float* py, const float* pz, double weight, double charge,
-                                  double mass) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (species != PIC_ELECTRON && species != PIC_ION) return fail(s, PIC_ERR_INVALID_ARG, "bad species");
-    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "load_particles after the first step");
-    if (s->sp[species].loaded) return fail(s, PIC_ERR_STATE, "species already loaded");
-    if (n < 0 || n > 2147483647LL - 64) return fail(s, PIC_ERR_INVALID_ARG, "n must be in [0, 2^31 - 64]");
-    if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(s, PIC_ERR_INVALID_ARG, "NULL array");
-    if (!(mass > 0.0) || !std::isfinite(weight) || !std::isfinite(charge))
-        return fail(s, PIC_ERR_INVALID_ARG, "mass must be > 0, weight and charge finite");
-    bool sorted = true;
-    for (int64_t i = 0; i < n; ++i) {
-        if (cell[i] < 0 || cell[i] >= s->Nx) return fail(s, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
-        if (!(off[i] >= 0.0f && off[i] < 1.0f)) return fail(s, PIC_ERR_INVALID_ARG, "offset out of [0, 1)");
-        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]))
-            return fail(s, PIC_ERR_INVALID_ARG, "non-finite momentum");
-        if (i > 0 && cell[i] < cell[i - 1]) sorted = false;
-    }
-    if (!sorted) {
-        std::vector<double> o(off, off + n), x(px, px + n), y(py, py + n), z(pz, pz + n);
-        return pic_load_particles(s, species, n, cell, o.data(), x.data(), y.data(), z.data(), weight, charge,
-                                  mass);
-    }
-    DeviceGuard g(s->device);
-    std::vector<void*> fresh;
-    HostSpecies h;
-    pic_status st = alloc_species(s, h, n, fresh);
-    if (st != PIC_OK) {
-        release(s, fresh);
-        return st;
-    }
-    const DevSpecies& d = h.buf[0];
-    const size_t b4 = static_cast<size_t>(n) * 4;
-    cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        e = cudaMemcpyAsync(d.cell, cell, b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.off, off, b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.px, px, b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.py, py, b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d.pz, pz, b4, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) {
-            launch_iota(d.id, n, s->stream);
-            s->launches++;
-        }
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        release(s, fresh);
-        return cuda_fail(s, e, "upload particles");
-    }
-    h.w = weight;
-    h.q = charge;
-    h.m = mass;
-    h.loaded = true;
-    s->sp[species] = h;
-    return PIC_OK;
-}
-
-pic_status pic_set_fields(pic_sim* s, const double* Ex, const double* Ey, const double* Ez, const double* By,
-                          const double* Bz) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "set_fields after the first step");
-    if (s->fields_set) return fail(s, PIC_ERR_STATE, "fields already set");
-    const double* src[5] = {Ex, Ey, Ez, By, Bz};
-    std::vector<float> h(s->glen);
-    DeviceGuard g(s->device);
+pic_status run_set_fields(Batch* b, int id, const double* const* src) {
+    RunHost& r = b->runs[id];
+    if (r.started) return fail(b, PIC_ERR_STATE, "set_fields after the first step");
+    if (r.fields_set) return fail(b, PIC_ERR_STATE, "fields already set");
+    std::vector<float> h(r.glen);
     for (int c = 0; c < 5; ++c) {
         std::fill(h.begin(), h.end(), 0.0f);
-        const int n = (c == 1 || c == 2) ? s->Nx + 1 : s->Nx;
+        const int n = (c == 1 || c == 2) ? r.Nx + 1 : r.Nx;
         if (src[c])
             for (int i = 0; i < n; ++i) {
-                if (!std::isfinite(src[c][i])) return fail(s, PIC_ERR_INVALID_ARG, "non-finite field value");
+                if (!std::isfinite(src[c][i])) return fail(b, PIC_ERR_INVALID_ARG, "non-finite field value");
                 h[PADF + i] = static_cast<float>(src[c][i]);
             }
-        PIC_CK(s, cudaMemcpyAsync(s->F[s->fcur][c], h.data(), s->glen * 4, cudaMemcpyHostToDevice, s->stream));
-        PIC_CK(s, cudaStreamSynchronize(s->stream));
+        // a run's fields start in buffer 0 (its parity offset makes that current)
+        PIC_CK(b, cudaMemcpyAsync(r.dev.F[0][c], h.data(), r.glen * 4, cudaMemcpyHostToDevice, b->stream));
+        PIC_CK(b, cudaStreamSynchronize(b->stream));
     }
-    s->fields_set = true;
+    r.fields_set = true;
     return PIC_OK;
 }
 
-pic_status pic_inject_laser(pic_sim* s, double a0, int polarization, int envelope, double duration_periods,
-                            double rise_periods) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (!before_first_step(s)) return fail(s, PIC_ERR_STATE, "inject_laser after the first step");
-    if (s->laser_set) return fail(s, PIC_ERR_STATE, "laser already set");
-    if (!(a0 >= 0.0 && std::isfinite(a0))) return fail(s, PIC_ERR_INVALID_ARG, "a0 must be finite and >= 0");
-    if (polarization != PIC_LP && polarization != PIC_CP) return fail(s, PIC_ERR_INVALID_ARG, "bad polarization");
-    if (envelope != PIC_ENV_SIN2 && envelope != PIC_ENV_TRAPEZOID) return fail(s, PIC_ERR_INVALID_ARG, "bad envelope");
-    if (!(duration_periods > 0.0 && std::isfinite(duration_periods)))
-        return fail(s, PIC_ERR_INVALID_ARG, "duration must be > 0");
-    if (envelope == PIC_ENV_TRAPEZOID && !(rise_periods > 0.0 && 2.0 * rise_periods <= duration_periods))
-        return fail(s, PIC_ERR_INVALID_ARG, "trapezoid needs 0 < 2 rise <= duration");
-    s->laser.on = 1;
-    s->laser.pol = polarization;
-    s->laser.env = envelope;
-    s->laser.a0 = a0;
-    s->laser.tau = duration_periods * 2.0 * kPi;
-    s->laser.rise = rise_periods * 2.0 * kPi;
-    s->laser_set = true;
+// Fixed-point scales and per-species constants of a run, frozen at its first step.
+void finalize_run_params(Batch* b, RunHost& r) {
+    RunDev& d = r.dev;
+    double bound = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        const HostSpecies& h = r.sp[s];
+        d.n[s] = h.loaded ? static_cast<int32_t>(h.n) : 0;
+        d.qm[s] = h.loaded ? static_cast<float>(h.q / h.m) : 0.f;
+        d.qw[s] = h.loaded ? static_cast<float>(h.q * h.w) : 0.f;
+        d.rad_w[s] = h.loaded ? static_cast<float>(h.w * b->dx * h.m) : 0.f;
+        if (h.loaded) bound += static_cast<double>(h.n) * std::fabs(h.q * h.w) / b->cfl;
+    }
+    // every partial sum of the current is bounded by `bound`: keep bound * 2^fp below 2^61
+    int fp = 40;
+    if (bound > 0.0) fp = static_cast<int>(std::floor(61.0 - std::log2(bound)));
+    r.fp_bits = std::max(8, std::min(52, fp));
+    d.fp_inv = std::ldexp(1.0f, -r.fp_bits);
+    for (int s = 0; s < 2; ++s) {
+        // a warp record sums at most 16 particles of one lane (a thread holds at most
+        // UNIT_P / PUSH_T + 4 particles of a unit) over 32 lanes, each value bounded by
+        // |q w| max(1, 1/cfl): keep every lane below 2^26
+        static_assert(UNIT_P / PUSH_T + 4 <= 16, "running record bound");
+        const double vmax = r.sp[s].loaded ? std::fabs(r.sp[s].q * r.sp[s].w) * std::max(1.0, 1.0 / b->cfl) : 0.0;
+        int ls = 40;
+        if (vmax > 0.0) ls = static_cast<int>(std::floor(26.0 - std::log2(16.0 * vmax)));
+        ls = std::min(ls, r.fp_bits);
+        d.lscale[s] = std::ldexp(1.0f, ls);
+        d.lshift[s] = std::min(62, r.fp_bits - ls);
+    }
+    d.rr = r.rr;
+}
+
+// Grow the batch-level unit table and sort scratch to hold `need` units.
+pic_status ensure_units(Batch* b, int need) {
+    if (need <= b->max_units) return PIC_OK;
+    const int mu = std::max(need, b->max_units + b->max_units / 2);
+    std::vector<std::pair<void*, size_t>> fresh;
+    UnitTable u{};
+    double* rp = nullptr;
+    int32_t *cn = nullptr, *of = nullptr;
+    const size_t m = static_cast<size_t>(mu);
+    pic_status st = PIC_OK;
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.run, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.species, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.start, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.end, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.lo, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.hi, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &u.count, 4);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &rp, m);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &cn, m * SSTR);
+    if (st == PIC_OK) st = dalloc_t(b, fresh, &of, m * SSTR);
+    if (st != PIC_OK) {
+        free_all(b, fresh);
+        return st;
+    }
+    // the unit table is rebuilt right after every growth (the radiated partials
+    // were flushed by the sort that preceded it)
+    for (void* p : {static_cast<void*>(b->units.run), static_cast<void*>(b->units.species),
+                    static_cast<void*>(b->units.start), static_cast<void*>(b->units.end),
+                    static_cast<void*>(b->units.lo), static_cast<void*>(b->units.hi),
+                    static_cast<void*>(b->units.count), static_cast<void*>(b->rad_part), static_cast<void*>(b->cnt),
+                    static_cast<void*>(b->offs)})
+        free_one(b, p);
+    for (auto& f : fresh) b->mem.push_back(f);
+    b->units = u;
+    b->rad_part = rp;
+    b->cnt = cn;
+    b->offs = of;
+    b->max_units = mu;
     return PIC_OK;
 }
 
-// Add the per-unit radiated energy into the tally (before the units change).
-static void rad_flush(pic_sim* s) {
-    launch_rad_flush(s->rad_part, s->units.count, s->tally, s->stream);
-    s->launches++;
+SortParams sort_params(Batch* b) {
+    SortParams S{};
+    S.runs = b->d_runs;
+    S.nruns = b->max_runs;
+    S.units = b->units;
+    S.cnt = b->cnt;
+    S.offs = b->offs;
+    S.rs_units = b->rs_units;
+    S.status = b->d_status;
+    S.k = b->since_sort;
+    S.cur = b->cur;
+    S.max_units = b->max_units;
+    int mx = 1;
+    for (auto& r : b->runs)
+        if (r.used) mx = std::max(mx, r.Nx);
+    S.kb_max = (mx + KEY_T - 1) / KEY_T;
+    return S;
 }
 
-static pic_status do_sort(pic_sim* s) {
-    SortParams S = sort_params(s);
-    int nl = 0;
-    {
-        Timed t(s, 2);
-        rad_flush(s);
-        launch_sort(S, s->max_units, s->stream, &nl);
-    }
-    s->launches += nl;
-    for (int k = 0; k < 2; ++k) s->sp[k].cur ^= 1;
-    s->sorts++;
-    s->since_sort = 0;
-    return PIC_OK;
-}
-
-pic_status pic_step_n(pic_sim* s, int64_t n, int64_t* steps_done) {
-    if (steps_done) *steps_done = 0;
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (n < 0) return fail(s, PIC_ERR_INVALID_ARG, "n must be >= 0");
-    DeviceGuard g(s->device);
-    if (!s->prepared) {
-        pic_status st = prepare(s);
-        if (st != PIC_OK) return st;
-    }
-    const int fgrid = (s->Nx + 1 + FIELD_T - 1) / FIELD_T;
-    for (int64_t it = 0; it < n; ++it) {
-        {
-            Timed t(s, 0);
-            launch_push(push_params(s), s->max_units, s->stream);
-        }
-        {
-            Timed t(s, 1);
-            launch_field(field_params(s), fgrid, s->stream);
-        }
-        s->launches += 2;
-        s->push_launches++;
-        s->fcur ^= 1;
-        s->step++;
-        s->since_sort++;
-        if (s->since_sort >= s->sort_interval) do_sort(s);
-        if ((it & 255) == 255) {  // keep the host from running far ahead; surface launch errors early
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
-        }
-    }
-    if (n > 0 && s->since_sort > 0) rad_flush(s);
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(s, e, "step");
-    collect_timing(s);
-    int hst[1] = {0}, meta[8] = {0};
-    PIC_CK(s, cudaMemcpy(hst, s->status, sizeof(int), cudaMemcpyDeviceToHost));
-    PIC_CK(s, cudaMemcpy(meta, s->meta, sizeof(meta), cudaMemcpyDeviceToHost));
-    if (steps_done) *steps_done = n;
-    if (hst[0] & ST_TIMEOUT) return fail(s, PIC_ERR_TIMEOUT, "a bounded device wait (TMA field window) gave up");
-    if ((hst[0] | meta[4]) & ST_WINDOW) return fail(s, PIC_ERR_STATE, "a particle left its unit window");
-    return PIC_OK;
-}
-
-pic_status pic_energy(pic_sim* s, double out[6]) {
-    if (!s || !out) return s ? fail(s, PIC_ERR_INVALID_ARG, "out is NULL") : PIC_ERR_INVALID_ARG;
-    DeviceGuard g(s->device);
-    DiagParams D{};
-    for (int c = 0; c < 5; ++c) D.F[c] = s->F[s->fcur][c];
-    D.Nx = s->Nx;
-    D.is = s->is;
-    D.hc = static_cast<float>(0.5 * s->cfl);
-    int nb = launch_field_energy(D, s->diag_partials, kMaxDiagBlocks, s->stream);
-    launch_reduce_partials(s->diag_partials, nb, s->dx, s->diag_out + 0, s->stream);
-    s->launches += 2;
-    for (int k = 0; k < 2; ++k) {
-        const HostSpecies& h = s->sp[k];
-        if (!h.loaded || h.n == 0) {
-            PIC_CK(s, cudaMemsetAsync(s->diag_out + 1 + k, 0, sizeof(double), s->stream));
+// Upload the run table (pointers, constants, active flags).
+pic_status upload_table(Batch* b) {
+    if (!b->table_dirty) return PIC_OK;
+    for (int i = 0; i < b->max_runs; ++i) {
+        const RunHost& r = b->runs[i];
+        if (!r.used) {
+            std::memset(&b->h_runs[i], 0, sizeof(RunDev));
             continue;
         }
-        nb = launch_kinetic(h.buf[h.cur], h.n, s->diag_partials, kMaxDiagBlocks, s->stream);
-        launch_reduce_partials(s->diag_partials, nb, h.w * s->dx * h.m, s->diag_out + 1 + k, s->stream);
-        s->launches += 2;
+        RunDev d = r.dev;
+        d.active = r.active ? 1 : 0;
+        b->h_runs[i] = d;
+    }
+    PIC_CK(b, cudaMemcpyAsync(b->d_runs, b->h_runs, sizeof(RunDev) * b->max_runs, cudaMemcpyHostToDevice,
+                              b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));  // the pinned staging is rewritten by the next upload
+    b->table_dirty = false;
+    return PIC_OK;
+}
+
+// Block table of the Yee kernel: FIELD_T nodes of one active run per block.
+pic_status upload_blocks(Batch* b) {
+    if (!b->layout_dirty) return PIC_OK;
+    std::vector<int32_t> br, bi;
+    for (int i = 0; i < b->max_runs; ++i) {
+        const RunHost& r = b->runs[i];
+        if (!r.used || !r.active) continue;
+        for (int i0 = 0; i0 <= r.Nx; i0 += FIELD_T) {
+            br.push_back(i);
+            bi.push_back(i0);
+        }
+    }
+    const int n = static_cast<int>(br.size());
+    if (n > b->blk_cap) {
+        std::vector<std::pair<void*, size_t>> fresh;
+        int32_t *a = nullptr, *c = nullptr;
+        pic_status st = dalloc_t(b, fresh, &a, static_cast<size_t>(n));
+        if (st == PIC_OK) st = dalloc_t(b, fresh, &c, static_cast<size_t>(n));
+        if (st != PIC_OK) {
+            free_all(b, fresh);
+            return st;
+        }
+        free_one(b, b->d_blk_run);
+        free_one(b, b->d_blk_i0);
+        for (auto& f : fresh) b->mem.push_back(f);
+        b->d_blk_run = a;
+        b->d_blk_i0 = c;
+        b->blk_cap = n;
+    }
+    if (n > 0) {
+        PIC_CK(b, cudaMemcpyAsync(b->d_blk_run, br.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(b->d_blk_i0, bi.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->stream));
+        PIC_CK(b, cudaStreamSynchronize(b->stream));
+    }
+    b->nblk = n;
+    b->layout_dirty = false;
+    return PIC_OK;
+}
+
+void rad_flush(Batch* b) {
+    if (b->max_units == 0) return;
+    launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, b->stream);
+    b->launches++;
+}
+
+void do_sort(Batch* b) {
+    SortParams S = sort_params(b);
+    int nl = 0;
+    {
+        Timed t(b, 2);
+        rad_flush(b);
+        launch_sort(S, b->stream, &nl);
+    }
+    b->launches += nl;
+    b->cur ^= 1;
+    b->sorts++;
+    b->since_sort = 0;
+}
+
+// Start runs that have not stepped yet.  They join at a sort boundary, so
+// that every active run's particles are sorted when the unit table is rebuilt
+// (their own particles were loaded in cell order into the current buffer).
+pic_status activate_pending(Batch* b) {
+    bool any = false;
+    for (auto& r : b->runs)
+        if (r.used && !r.started) any = true;
+    if (!any) return PIC_OK;
+    pic_status st = upload_table(b);  // the sort below reads the device run table
+    if (st != PIC_OK) return st;
+    if (b->since_sort > 0) {
+        do_sort(b);
+        // runs loaded before this sort have their particles in the old buffer
+        for (auto& r : b->runs)
+            if (r.used && !r.started)
+                for (int s = 0; s < 2; ++s) std::swap(r.dev.sp[s][0], r.dev.sp[s][1]);
+    }
+    // units the active and the joining runs can need (each tile adds at most one partial unit)
+    int64_t need = 1;
+    std::vector<int> joining;
+    for (int i = 0; i < b->max_runs; ++i) {
+        const RunHost& r = b->runs[i];
+        if (!r.used || r.finished || (r.started && !r.active)) continue;
+        if (!r.started) joining.push_back(i);
+        const int ntiles = (r.Nx + TILE - 1) / TILE;
+        for (int s = 0; s < 2; ++s)
+            if (r.sp[s].loaded) need += (r.sp[s].n + UNIT_P - 1) / UNIT_P + ntiles + 1;
+    }
+    if (need > (1 << 30)) return fail(b, PIC_ERR_INVALID_ARG, "too many work units");
+    st = ensure_units(b, static_cast<int>(need));
+    if (st != PIC_OK) return st;  // the joining runs stay pending
+    for (int i : joining) {
+        RunHost& r = b->runs[i];
+        finalize_run_params(b, r);
+        r.started = true;
+        r.active = true;
+        r.admit_step = b->gstep;
+        r.dev.fpar = static_cast<int>(b->gstep & 1);  // buffer 0 is current at the first step
+    }
+    b->table_dirty = b->layout_dirty = true;
+    st = upload_blocks(b);
+    if (st != PIC_OK) {
+        for (int i : joining) b->runs[i].started = b->runs[i].active = false;
+        return st;
+    }
+    if ((st = upload_table(b)) != PIC_OK) return st;
+    SortParams S = sort_params(b);
+    int nl = 0;
+    launch_build_units(S, b->stream, &nl);
+    b->launches += nl;
+    return PIC_OK;
+}
+
+void deactivate(Batch* b, int id) {
+    RunHost& r = b->runs[id];
+    r.active = false;
+    r.finished = true;
+    r.pbuf = b->cur;
+    r.fbuf = static_cast<int>((b->gstep + r.dev.fpar) & 1);
+    b->table_dirty = b->layout_dirty = true;
+}
+
+// Laser source values of the coming step for every active run, uploaded
+// through a pinned ring.
+pic_status upload_incident(Batch* b) {
+    float* h = b->h_inc + static_cast<size_t>(b->inc_slot) * 6 * b->max_runs;
+    PIC_CK(b, cudaEventSynchronize(b->inc_ev[b->inc_slot]));
+    int hi = -1;
+    for (int i = 0; i < b->max_runs; ++i) {
+        const RunHost& r = b->runs[i];
+        if (!r.used || !r.active) continue;
+        hi = i;
+        const double tn = static_cast<double>(b->gstep - r.admit_step) * b->dt;
+        const double ts[3] = {tn, tn + 0.5 * b->dt + 0.5 * b->dx, tn + b->dt};
+        for (int k = 0; k < 3; ++k) incident(r.laser, ts[k], &h[6 * i + 2 * k], &h[6 * i + 2 * k + 1]);
+    }
+    if (hi >= 0)
+        PIC_CK(b, cudaMemcpyAsync(b->d_inc, h, sizeof(float) * 6 * (hi + 1), cudaMemcpyHostToDevice, b->stream));
+    cudaEventRecord(b->inc_ev[b->inc_slot], b->stream);
+    b->inc_slot = (b->inc_slot + 1) % kIncRing;
+    return PIC_OK;
+}
+
+pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
+    if (done) *done = 0;
+    pic_status st = activate_pending(b);
+    if (st != PIC_OK) return st;
+    if ((st = upload_table(b)) != PIC_OK) return st;
+    if ((st = upload_blocks(b)) != PIC_OK) return st;
+    int64_t it = 0;
+    for (; it < n; ++it) {
+        int nact = 0;
+        for (auto& r : b->runs) nact += (r.used && r.active) ? 1 : 0;
+        if (nact == 0) break;
+        if ((st = upload_incident(b)) != PIC_OK) return st;
+        PushParams P{};
+        P.runs = b->d_runs;
+        P.units = b->units;
+        P.rad_part = b->rad_part;
+        P.status = b->d_status;
+        P.gstep = b->gstep;
+        P.k = b->since_sort;
+        P.cur = b->cur;
+        P.cfl = static_cast<float>(b->cfl);
+        P.dt = static_cast<float>(b->dt);
+        P.eps = static_cast<float>(b->eps);
+        FieldParams Q{};
+        Q.runs = b->d_runs;
+        Q.blk_run = b->d_blk_run;
+        Q.blk_i0 = b->d_blk_i0;
+        Q.inc = b->d_inc;
+        Q.gstep = b->gstep;
+        Q.dt = b->dt;
+        Q.c = static_cast<float>(b->cfl);
+        Q.hc = static_cast<float>(0.5 * b->cfl);
+        Q.fdt = static_cast<float>(b->dt);
+        {
+            Timed t(b, 0);
+            launch_push(P, b->max_units, b->stream);
+        }
+        {
+            Timed t(b, 1);
+            launch_field(Q, b->nblk, b->stream);
+        }
+        b->launches += 2;
+        b->push_launches++;
+        b->gstep++;
+        b->since_sort++;
+        bool ended = false;
+        for (auto& r : b->runs) {
+            if (!r.used || !r.active) continue;
+            r.steps_done++;
+            if (r.steps_target > 0 && r.steps_done >= r.steps_target) ended = true;
+        }
+        if (ended) {
+            rad_flush(b);  // finished runs take their radiated energy with them
+            for (int i = 0; i < b->max_runs; ++i) {
+                RunHost& r = b->runs[i];
+                if (r.used && r.active && r.steps_target > 0 && r.steps_done >= r.steps_target) deactivate(b, i);
+            }
+            if ((st = upload_table(b)) != PIC_OK) return st;
+            if ((st = upload_blocks(b)) != PIC_OK) return st;
+        }
+        if (b->since_sort >= b->sort_interval) do_sort(b);
+        if ((it & 255) == 255) {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(b, e, "step launch");
+        }
+    }
+    if (it > 0 && b->since_sort > 0) rad_flush(b);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(b, e, "step");
+    collect_timing(b);
+    int hst = 0;
+    PIC_CK(b, cudaMemcpy(&hst, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (done) *done = it;
+    if (hst & ST_TIMEOUT) return fail(b, PIC_ERR_TIMEOUT, "a bounded device wait (TMA field window) gave up");
+    if (hst & ST_WINDOW) return fail(b, PIC_ERR_STATE, "a particle left its unit window");
+    return PIC_OK;
+}
+
+// particle buffer and field buffer holding a run's current state
+int run_pbuf(const Batch* b, const RunHost& r) { return r.finished ? r.pbuf : b->cur; }
+int run_fbuf(const Batch* b, const RunHost& r) {
+    if (r.finished) return r.fbuf;
+    if (!r.started) return 0;
+    return static_cast<int>((b->gstep + r.dev.fpar) & 1);
+}
+
+pic_status run_energy(Batch* b, int id, double out[6]) {
+    const RunHost& r = b->runs[id];
+    DiagParams D{};
+    const int fb = run_fbuf(b, r);
+    for (int c = 0; c < 5; ++c) D.F[c] = r.dev.F[fb][c];
+    D.Nx = r.Nx;
+    D.is = r.is;
+    D.hc = static_cast<float>(0.5 * b->cfl);
+    int nb = launch_field_energy(D, b->diag_partials, kMaxDiagBlocks, b->stream);
+    launch_reduce_partials(b->diag_partials, nb, b->dx, b->diag_out + 0, b->stream);
+    b->launches += 2;
+    for (int s = 0; s < 2; ++s) {
+        const HostSpecies& h = r.sp[s];
+        if (!h.loaded || h.n == 0) {
+            PIC_CK(b, cudaMemsetAsync(b->diag_out + 1 + s, 0, sizeof(double), b->stream));
+            continue;
+        }
+        nb = launch_kinetic(r.dev.sp[s][run_pbuf(b, r)], h.n, b->diag_partials, kMaxDiagBlocks, b->stream);
+        launch_reduce_partials(b->diag_partials, nb, h.w * b->dx * h.m, b->diag_out + 1 + s, b->stream);
+        b->launches += 2;
     }
     double d[3], t[3];
-    PIC_CK(s, cudaMemcpyAsync(d, s->diag_out, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(t, s->tally, sizeof(t), cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaStreamSynchronize(s->stream));
+    PIC_CK(b, cudaMemcpyAsync(d, b->diag_out, sizeof(d), cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(t, r.dev.tally, sizeof(t), cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));
     out[0] = d[0];
     out[1] = d[1];
     out[2] = d[2];
@@ -815,83 +1038,82 @@ pic_status pic_energy(pic_sim* s, double out[6]) {
     return PIC_OK;
 }
 
-pic_status pic_spectra(pic_sim* s, int species, int nbins, double e_min, double e_max, double* counts,
+pic_status run_spectra(Batch* b, int id, int species, int nbins, double e_min, double e_max, double* counts,
                        double* radiated) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (species != PIC_ELECTRON && species != PIC_ION) return fail(s, PIC_ERR_INVALID_ARG, "bad species");
+    if (species != PIC_ELECTRON && species != PIC_ION) return fail(b, PIC_ERR_INVALID_ARG, "bad species");
     if (nbins < 1 || nbins > (1 << 24) || !counts || !(e_max > e_min) || !std::isfinite(e_min) ||
         !std::isfinite(e_max))
-        return fail(s, PIC_ERR_INVALID_ARG, "need 1 <= nbins <= 2^24, e_max > e_min, counts != NULL");
-    DeviceGuard g(s->device);
-    const HostSpecies& h = s->sp[species];
+        return fail(b, PIC_ERR_INVALID_ARG, "need 1 <= nbins <= 2^24, e_max > e_min, counts != NULL");
+    const RunHost& r = b->runs[id];
+    const HostSpecies& h = r.sp[species];
     std::vector<unsigned long long> hb(static_cast<size_t>(nbins) + 2, 0ull);
     if (h.loaded && h.n > 0) {
-        if (s->bins_cap < nbins + 2) {
-            if (s->bins) dfree(s, s->bins);
-            s->bins = nullptr;
-            s->bins_cap = 0;
-            pic_status st = dalloc_t(s, &s->bins, static_cast<size_t>(nbins) + 2, nullptr);
+        if (b->bins_cap < nbins + 2) {
+            std::vector<std::pair<void*, size_t>> fresh;
+            unsigned long long* nbp = nullptr;
+            pic_status st = dalloc_t(b, fresh, &nbp, static_cast<size_t>(nbins) + 2);
             if (st != PIC_OK) return st;
-            s->bins_cap = nbins + 2;
+            free_one(b, b->bins);
+            b->mem.push_back(fresh[0]);
+            b->bins = nbp;
+            b->bins_cap = nbins + 2;
         }
-        PIC_CK(s, cudaMemsetAsync(s->bins, 0, sizeof(unsigned long long) * (nbins + 2), s->stream));
-        launch_spectrum(h.buf[h.cur], h.n, h.m * kMec2MeV, nbins, e_min, e_max, s->bins, s->stream);
-        s->launches++;
-        PIC_CK(s, cudaMemcpyAsync(hb.data(), s->bins, sizeof(unsigned long long) * (nbins + 2),
-                                  cudaMemcpyDeviceToHost, s->stream));
+        PIC_CK(b, cudaMemsetAsync(b->bins, 0, sizeof(unsigned long long) * (nbins + 2), b->stream));
+        launch_spectrum(r.dev.sp[species][run_pbuf(b, r)], h.n, h.m * kMec2MeV, nbins, e_min, e_max, b->bins,
+                        b->stream);
+        b->launches++;
+        PIC_CK(b, cudaMemcpyAsync(hb.data(), b->bins, sizeof(unsigned long long) * (nbins + 2),
+                                  cudaMemcpyDeviceToHost, b->stream));
     }
     double tally0 = 0.0;
-    PIC_CK(s, cudaMemcpyAsync(&tally0, s->tally, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaStreamSynchronize(s->stream));
+    PIC_CK(b, cudaMemcpyAsync(&tally0, r.dev.tally, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));
     const double width = (e_max - e_min) / nbins;
-    const double wdx = h.w * s->dx;
+    const double wdx = h.w * b->dx;
     for (int k = 0; k < nbins; ++k) counts[k] = static_cast<double>(hb[k]) * wdx / width;
     if (radiated) {
         // energy unit per area: m_e c^2 n_c (c/omega), n_c = eps0 m_e omega^2 / e^2 (SI)
         const double me = 9.1093837015e-31, c = 299792458.0, qe = 1.602176634e-19, eps0 = 8.8541878128e-12;
-        const double omega = 2.0 * kPi * c / (s->cfg.lambda_um * 1e-6);
+        const double omega = 2.0 * kPi * c / (b->cfg.lambda_um * 1e-6);
         const double nc = eps0 * me * omega * omega / (qe * qe);
         *radiated = tally0 * me * c * c * nc * c / omega;
     }
     return PIC_OK;
 }
 
-pic_status pic_read_particles(pic_sim* s, int species, int64_t cap, double* x, double* px, double* py, double* pz,
-                              int32_t* flag, int64_t* nout) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (species != PIC_ELECTRON && species != PIC_ION) return fail(s, PIC_ERR_INVALID_ARG, "bad species");
-    const HostSpecies& h = s->sp[species];
+pic_status run_read_particles(Batch* b, int id, int species, int64_t cap, double* x, double* px, double* py,
+                              double* pz, int32_t* flag, int64_t* nout) {
+    if (species != PIC_ELECTRON && species != PIC_ION) return fail(b, PIC_ERR_INVALID_ARG, "bad species");
+    const RunHost& r = b->runs[id];
+    const HostSpecies& h = r.sp[species];
     const int64_t n = h.loaded ? h.n : 0;
     if (nout) *nout = n;
     if (cap <= 0 || n == 0) return PIC_OK;
-    DeviceGuard g(s->device);
-    std::vector<int32_t> c(n), id(n);
+    std::vector<int32_t> c(n), idv(n);
     std::vector<float> o(n), qx(n), qy(n), qz(n);
-    const DevSpecies& d = h.buf[h.cur];
-    const size_t b = static_cast<size_t>(n) * 4;
-    PIC_CK(s, cudaMemcpyAsync(c.data(), d.cell, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(id.data(), d.id, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(o.data(), d.off, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(qx.data(), d.px, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(qy.data(), d.py, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaMemcpyAsync(qz.data(), d.pz, b, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaStreamSynchronize(s->stream));
+    const DevSpecies& d = r.dev.sp[species][run_pbuf(b, r)];
+    const size_t by = static_cast<size_t>(n) * 4;
+    PIC_CK(b, cudaMemcpyAsync(c.data(), d.cell, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(idv.data(), d.id, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(o.data(), d.off, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(qx.data(), d.px, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(qy.data(), d.py, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(qz.data(), d.pz, by, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));
     for (int64_t i = 0; i < n; ++i) {
-        const int64_t j = id[i];
-        if (j < 0 || j >= n) return fail(s, PIC_ERR_STATE, "corrupt particle id");
+        const int64_t j = idv[i];
+        if (j < 0 || j >= n) return fail(b, PIC_ERR_STATE, "corrupt particle id");
         if (j >= cap) continue;
         int fl = 0;
         double xi;
-        if (c[i] == -1) {
-            xi = 0.0;
-            fl = -1;
-        } else if (c[i] == -2) {
-            xi = s->Nx;
-            fl = 1;
+        if (c[i] < 0) {  // frozen at a wall, stored as -1 - (last cell)
+            const int key = -1 - c[i];
+            fl = key == 0 ? -1 : 1;
+            xi = key == 0 ? 0.0 : static_cast<double>(r.Nx);
         } else {
             xi = static_cast<double>(c[i]) + o[i];
         }
-        if (x) x[j] = xi * s->dx;
+        if (x) x[j] = xi * b->dx;
         if (px) px[j] = qx[i];
         if (py) py[j] = qy[i];
         if (pz) pz[j] = qz[i];
@@ -900,79 +1122,373 @@ pic_status pic_read_particles(pic_sim* s, int species, int64_t cap, double* x, d
     return PIC_OK;
 }
 
-pic_status pic_read_fields(pic_sim* s, int comp, int64_t cap, double* out, int64_t* nout) {
-    if (!s) return PIC_ERR_INVALID_ARG;
-    if (comp < PIC_EX || comp > PIC_JZ) return fail(s, PIC_ERR_INVALID_ARG, "bad component");
+pic_status run_read_fields(Batch* b, int id, int comp, int64_t cap, double* out, int64_t* nout) {
+    if (comp < PIC_EX || comp > PIC_JZ) return fail(b, PIC_ERR_INVALID_ARG, "bad component");
+    const RunHost& r = b->runs[id];
     const bool node = comp == PIC_EY || comp == PIC_EZ || comp == PIC_JY || comp == PIC_JZ;
-    const int64_t n = node ? s->Nx + 1 : s->Nx;
+    const int64_t n = node ? r.Nx + 1 : r.Nx;
     if (nout) *nout = n;
-    if (!out || cap < n) return fail(s, PIC_ERR_INVALID_ARG, "output too small");
-    DeviceGuard g(s->device);
-    const float* src = comp <= PIC_BZ ? s->F[s->fcur][comp] : s->Jf[comp - PIC_JX];
+    if (!out || cap < n) return fail(b, PIC_ERR_INVALID_ARG, "output too small");
+    const float* src = comp <= PIC_BZ ? r.dev.F[run_fbuf(b, r)][comp] : r.dev.Jf[comp - PIC_JX];
     std::vector<float> h(static_cast<size_t>(n));
-    PIC_CK(s, cudaMemcpyAsync(h.data(), src + PADF, sizeof(float) * n, cudaMemcpyDeviceToHost, s->stream));
-    PIC_CK(s, cudaStreamSynchronize(s->stream));
+    PIC_CK(b, cudaMemcpyAsync(h.data(), src + PADF, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));
     for (int64_t i = 0; i < n; ++i) out[i] = h[static_cast<size_t>(i)];
     return PIC_OK;
 }
 
+void fill_stats(Batch* b, pic_stats_t* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->steps = b->gstep;
+    out->kernel_launches = b->launches;
+    out->push_launches = b->push_launches;
+    out->sort_count = b->sorts;
+    out->push_ms = b->push_ms;
+    out->field_ms = b->field_ms;
+    out->sort_ms = b->sort_ms;
+    out->timed_push_launches = b->timed_push;
+    out->device_bytes = static_cast<int64_t>(b->bytes);
+    int64_t act = 0;
+    int fp = 0;
+    for (auto& r : b->runs) {
+        if (!r.used || r.finished) continue;
+        for (int s = 0; s < 2; ++s) act += r.sp[s].loaded ? r.sp[s].n : 0;
+        if (r.started) fp = r.fp_bits;
+    }
+    out->active_particles = act;
+    out->fp_bits = fp;
+    int32_t cnt = 0;
+    if (b->units.count && cudaMemcpy(&cnt, b->units.count, sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess)
+        out->n_units = cnt;
+}
+
+pic_status set_timing(Batch* b, int on) {
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    collect_timing(b);
+    b->timing = on != 0;
+    if (b->timing) {
+        b->push_ms = b->field_ms = b->sort_ms = 0.0;
+        b->timed_push = 0;
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+}  // namespace picrr
+
+using namespace picrr;
+
+// A single-run handle: a batch of one.
+struct pic_sim {
+    Batch* b = nullptr;
+};
+
+struct pic_batch {
+    Batch* b = nullptr;
+};
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// single run
+// ---------------------------------------------------------------------------
+
+pic_status pic_create(const pic_config* cfg, pic_sim** out) {
+    if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfg is NULL");
+    pic_status st = validate_common(cfg);
+    if (st != PIC_OK) return st;
+    const double ncell = cfg->length_lambda * cfg->cells_per_lambda;
+    if (!(cfg->length_lambda > 0.0) || !(ncell >= 16.0 && ncell <= 1.0e9))
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "Nx must be in [16, 1e9]");
+    const int Nx = static_cast<int>(std::llround(ncell));
+    const int is = cfg->source_node ? cfg->source_node : 8;
+    if (is < 2 || is > Nx - 4) return fail(nullptr, PIC_ERR_INVALID_ARG, "source_node must be in [2, Nx-4]");
+    Batch* b = nullptr;
+    if ((st = batch_create(cfg, 1, &b)) != PIC_OK) return st;
+    DeviceGuard g(b->device);
+    int id = -1;
+    st = run_open(b, cfg->length_lambda, is, cfg->rr_on, cfg->seed, &id);
+    if (st == PIC_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = cuda_fail(b, cudaGetLastError(), "create");
+    if (st != PIC_OK) {
+        g_null_error = b->err;
+        batch_destroy(b);
+        return st;
+    }
+    pic_sim* s = new pic_sim();
+    s->b = b;
+    *out = s;
+    return PIC_OK;
+}
+
+pic_status pic_set_stream(pic_sim* s, void* stream) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    cudaStreamSynchronize(s->b->stream);
+    s->b->stream = stream ? static_cast<cudaStream_t>(stream) : s->b->own_stream;
+    return PIC_OK;
+}
+
+pic_status pic_load_foil(pic_sim* s, double x0_lambda, double thickness_lambda, double ne_over_nc, int ion_Z,
+                         double ion_A, int ppc) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    pic_status st = run_load_foil(s->b, 0, x0_lambda, thickness_lambda, ne_over_nc, ion_Z, ion_A, ppc);
+    if (st != PIC_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s->b->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? PIC_OK : cuda_fail(s->b, e, "foil loader");
+}
+
+pic_status pic_load_particles(pic_sim* s, int species, int64_t n, const int32_t* cell, const double* off,
+                              const double* px, const double* py, const double* pz, double weight, double charge,
+                              double mass) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    Batch* b = s->b;
+    RunHost& r = b->runs[0];
+    pic_status st = check_species_args(b, r, species, n, weight, charge, mass);
+    if (st != PIC_OK) return st;
+    if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(b, PIC_ERR_INVALID_ARG, "NULL array");
+    std::vector<float> o(static_cast<size_t>(n)), x(static_cast<size_t>(n)), y(static_cast<size_t>(n)),
+        z(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]) || !std::isfinite(off[i]))
+            return fail(b, PIC_ERR_INVALID_ARG, "non-finite input");
+        o[i] = static_cast<float>(off[i]);
+        x[i] = static_cast<float>(px[i]);
+        y[i] = static_cast<float>(py[i]);
+        z[i] = static_cast<float>(pz[i]);
+    }
+    DeviceGuard g(b->device);
+    return run_load_particles_f32(b, 0, species, n, cell, o.data(), x.data(), y.data(), z.data(), weight, charge,
+                                  mass);
+}
+
+pic_status pic_load_particles_f32(pic_sim* s, int species, int64_t n, const int32_t* cell, const float* off,
+                                  const float* px, const float* py, const float* pz, double weight, double charge,
+                                  double mass) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return run_load_particles_f32(s->b, 0, species, n, cell, off, px, py, pz, weight, charge, mass);
+}
+
+pic_status pic_set_fields(pic_sim* s, const double* Ex, const double* Ey, const double* Ez, const double* By,
+                          const double* Bz) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    const double* src[5] = {Ex, Ey, Ez, By, Bz};
+    return run_set_fields(s->b, 0, src);
+}
+
+pic_status pic_inject_laser(pic_sim* s, double a0, int polarization, int envelope, double duration_periods,
+                            double rise_periods) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    return run_inject_laser(s->b, 0, a0, polarization, envelope, duration_periods, rise_periods);
+}
+
+pic_status pic_step_n(pic_sim* s, int64_t n, int64_t* steps_done) {
+    if (steps_done) *steps_done = 0;
+    if (!s) return PIC_ERR_INVALID_ARG;
+    if (n < 0) return fail(s->b, PIC_ERR_INVALID_ARG, "n must be >= 0");
+    DeviceGuard g(s->b->device);
+    return batch_step(s->b, n, steps_done);
+}
+
+pic_status pic_energy(pic_sim* s, double out[6]) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    if (!out) return fail(s->b, PIC_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(s->b->device);
+    return run_energy(s->b, 0, out);
+}
+
+pic_status pic_spectra(pic_sim* s, int species, int nbins, double e_min, double e_max, double* counts,
+                       double* radiated) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return run_spectra(s->b, 0, species, nbins, e_min, e_max, counts, radiated);
+}
+
+pic_status pic_read_particles(pic_sim* s, int species, int64_t cap, double* x, double* px, double* py, double* pz,
+                              int32_t* flag, int64_t* n) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return run_read_particles(s->b, 0, species, cap, x, px, py, pz, flag, n);
+}
+
+pic_status pic_read_fields(pic_sim* s, int comp, int64_t cap, double* out, int64_t* n) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return run_read_fields(s->b, 0, comp, cap, out, n);
+}
+
 pic_status pic_stats(pic_sim* s, pic_stats_t* out) {
     if (!s || !out) return PIC_ERR_INVALID_ARG;
-    DeviceGuard g(s->device);
-    std::memset(out, 0, sizeof(*out));
-    out->steps = s->step;
-    out->kernel_launches = s->launches;
-    out->push_launches = s->push_launches;
-    out->sort_count = s->sorts;
-    out->push_ms = s->push_ms;
-    out->field_ms = s->field_ms;
-    out->sort_ms = s->sort_ms;
-    out->timed_push_launches = s->timed_push;
-    out->device_bytes = static_cast<int64_t>(s->bytes);
-    out->fp_bits = s->fp_bits;
-    if (s->prepared) {
-        int32_t cnt[4] = {0}, meta[8] = {0};
-        PIC_CK(s, cudaMemcpyAsync(cnt, s->units.count, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
-        PIC_CK(s, cudaMemcpyAsync(meta, s->meta, sizeof(meta), cudaMemcpyDeviceToHost, s->stream));
-        PIC_CK(s, cudaStreamSynchronize(s->stream));
-        out->n_units = cnt[0];
-        out->active_particles = static_cast<int64_t>(meta[0]) + meta[1];
-    } else {
-        out->active_particles = (s->sp[0].loaded ? s->sp[0].n : 0) + (s->sp[1].loaded ? s->sp[1].n : 0);
-    }
+    DeviceGuard g(s->b->device);
+    cudaStreamSynchronize(s->b->stream);
+    fill_stats(s->b, out);
     return PIC_OK;
 }
 
 pic_status pic_set_timing(pic_sim* s, int on) {
     if (!s) return PIC_ERR_INVALID_ARG;
-    DeviceGuard g(s->device);
-    cudaStreamSynchronize(s->stream);
-    collect_timing(s);
-    s->timing = on != 0;
-    if (s->timing) {
-        s->push_ms = s->field_ms = s->sort_ms = 0.0;
-        s->timed_push = 0;
-    }
-    return PIC_OK;
+    return set_timing(s->b, on);
 }
 
-const char* pic_last_error(const pic_sim* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+const char* pic_last_error(const pic_sim* s) { return s ? s->b->err.c_str() : g_null_error.c_str(); }
 
 pic_status pic_destroy(pic_sim* s) {
     if (!s) return PIC_OK;
-    {
-        DeviceGuard g(s->device);
-        if (s->stream) cudaStreamSynchronize(s->stream);
-        for (EventPair& ep : s->pending) {
-            cudaEventDestroy(ep.a);
-            cudaEventDestroy(ep.b);
-        }
-        for (cudaEvent_t e : s->ev_free) cudaEventDestroy(e);
-        for (auto& a : s->allocs) cudaFree(a.first);
-        s->allocs.clear();
-        if (s->own_stream) cudaStreamDestroy(s->own_stream);
-    }
+    batch_destroy(s->b);
     delete s;
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch of runs
+// ---------------------------------------------------------------------------
+
+pic_status pic_batch_create(const pic_config* common, int max_runs, pic_batch** out) {
+    if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    Batch* b = nullptr;
+    pic_status st = batch_create(common, max_runs, &b);
+    if (st != PIC_OK) return st;
+    pic_batch* h = new pic_batch();
+    h->b = b;
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_stream(pic_batch* h, void* stream) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(h->b->device);
+    cudaStreamSynchronize(h->b->stream);
+    h->b->stream = stream ? static_cast<cudaStream_t>(stream) : h->b->own_stream;
+    return PIC_OK;
+}
+
+pic_status pic_batch_add_run(pic_batch* h, const pic_run_desc* d, int* run_id) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    Batch* b = h->b;
+    if (!d || !run_id) return fail(b, PIC_ERR_INVALID_ARG, "desc and run_id must not be NULL");
+    *run_id = -1;
+    if (d->steps < 1) return fail(b, PIC_ERR_INVALID_ARG, "steps must be >= 1");
+    DeviceGuard g(b->device);
+    int id = -1;
+    pic_status st = run_open(b, d->length_lambda, d->source_node, d->rr_on, d->seed, &id);
+    if (st != PIC_OK) return st;
+    if ((st = run_load_foil(b, id, d->foil_x0_lambda, d->foil_thickness_lambda, d->ne_over_nc, d->ion_Z, d->ion_A,
+                            d->ppc)) != PIC_OK ||
+        (st = run_inject_laser(b, id, d->a0, d->polarization, d->envelope, d->duration_periods,
+                               d->rise_periods)) != PIC_OK) {
+        run_release(b, id);
+        return st;
+    }
+    b->runs[id].steps_target = d->steps;
+    *run_id = id;
+    return PIC_OK;
+}
+
+pic_status pic_batch_run_footprint(const pic_batch* h, const pic_run_desc* d, size_t* bytes) {
+    // reads only the batch's configuration and reports errors through the
+    // calling thread's handle-less message, so it may run beside the batch's owner
+    if (!h) return PIC_ERR_INVALID_ARG;
+    if (!d || !bytes) return fail(nullptr, PIC_ERR_INVALID_ARG, "desc and bytes must not be NULL");
+    const double cpl = h->b->cfg.cells_per_lambda, ncell = d->length_lambda * cpl;
+    if (!(d->length_lambda > 0.0) || !(ncell >= 16.0 && ncell <= 1.0e9) || d->ppc < 1 ||
+        !(d->foil_thickness_lambda > 0.0) || !(d->foil_thickness_lambda * cpl < 1.0e9))
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "need 16 <= cells <= 1e9, ppc >= 1, thickness > 0");
+    const int64_t n = std::llround(d->foil_thickness_lambda * cpl) * static_cast<int64_t>(d->ppc);
+    *bytes = run_footprint(h->b, d->length_lambda, n);
+    return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch* h, int64_t n, int64_t* steps_done) {
+    if (steps_done) *steps_done = 0;
+    if (!h) return PIC_ERR_INVALID_ARG;
+    if (n < 0) return fail(h->b, PIC_ERR_INVALID_ARG, "n must be >= 0");
+    DeviceGuard g(h->b->device);
+    return batch_step(h->b, n, steps_done);
+}
+
+static pic_status check_run(pic_batch* h, int run) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    if (run < 0 || run >= h->b->max_runs || !h->b->runs[run].used)
+        return fail(h->b, PIC_ERR_INVALID_ARG, "no such run");
+    return PIC_OK;
+}
+
+pic_status pic_batch_run_status(pic_batch* h, int run, int64_t* steps_done, int* finished) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    const RunHost& r = h->b->runs[run];
+    if (steps_done) *steps_done = r.steps_done;
+    if (finished) *finished = r.finished ? 1 : 0;
+    return PIC_OK;
+}
+
+pic_status pic_batch_energy(pic_batch* h, int run, double out[6]) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    if (!out) return fail(h->b, PIC_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(h->b->device);
+    return run_energy(h->b, run, out);
+}
+
+pic_status pic_batch_spectra(pic_batch* h, int run, int species, int nbins, double e_min, double e_max,
+                             double* counts, double* radiated) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    DeviceGuard g(h->b->device);
+    return run_spectra(h->b, run, species, nbins, e_min, e_max, counts, radiated);
+}
+
+pic_status pic_batch_read_particles(pic_batch* h, int run, int species, int64_t cap, double* x, double* px,
+                                    double* py, double* pz, int32_t* flag, int64_t* n) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    DeviceGuard g(h->b->device);
+    return run_read_particles(h->b, run, species, cap, x, px, py, pz, flag, n);
+}
+
+pic_status pic_batch_read_fields(pic_batch* h, int run, int comp, int64_t cap, double* out, int64_t* n) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    DeviceGuard g(h->b->device);
+    return run_read_fields(h->b, run, comp, cap, out, n);
+}
+
+pic_status pic_batch_release_run(pic_batch* h, int run) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    Batch* b = h->b;
+    if (b->runs[run].active) return fail(b, PIC_ERR_STATE, "run is still stepping");
+    DeviceGuard g(b->device);
+    run_release(b, run);
+    return upload_table(b);
+}
+
+pic_status pic_batch_stats(pic_batch* h, pic_stats_t* out) {
+    if (!h || !out) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(h->b->device);
+    cudaStreamSynchronize(h->b->stream);
+    fill_stats(h->b, out);
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_timing(pic_batch* h, int on) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    return set_timing(h->b, on);
+}
+
+const char* pic_batch_last_error(const pic_batch* h) { return h ? h->b->err.c_str() : g_null_error.c_str(); }
+
+pic_status pic_batch_destroy(pic_batch* h) {
+    if (!h) return PIC_OK;
+    batch_destroy(h->b);
+    delete h;
     return PIC_OK;
 }
 

@@ -1,6 +1,11 @@
 // Internal layout, constants and device helpers of the picrr CUDA library.
 //
-// Data layout in HBM (one handle):
+// A batch holds R independent runs (a single simulation handle is a batch of
+// one).  The kernels of one step process all active runs of the batch in one
+// launch each; a device table of RunDev entries gives every run's arrays and
+// parameters.
+//
+// Data layout in HBM (per run):
 //   grid arrays   float, Nx+1+2*PADF elements (rounded up to 4), element
 //                 PADF holds node / half node 0; the guard elements are zero.
 //                 Ex, Ey, Ez, By, Bz are ping-ponged by the Yee kernel.
@@ -8,10 +13,13 @@
 //                 Jy, Jz (nodes), two sets alternating by step parity.
 //   particles     per species, structure of arrays, two buffers each
 //                 (ping-ponged by the sort): cell int32, off/px/py/pz float,
-//                 id int32.  cell < 0 marks a particle frozen at a wall
-//                 (-1: x = 0, -2: x = L).
-//   units         work units of at most UNIT_P consecutive particles whose
-//                 cells at the last sort lie in one tile of TILE cells.
+//                 id int32.  A particle that left the box is frozen at the
+//                 wall and stored with cell = -1 - k, k its last cell (0 at
+//                 x = 0, Nx-1 at x = L); it keeps sorting under k.
+// Per batch:
+//   units         work units of at most UNIT_P consecutive particles of one
+//                 run and species whose cells at the last sort lie in one
+//                 tile of TILE cells.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,6 +35,7 @@ constexpr int PUSH_T = 256;       // threads of the push kernel
 constexpr int WMAX = 144;         // window length bound in the push kernel (>= TILE + 2 KMAX + 10)
 constexpr int SSTR = TILE + 2 * KMAX + 4;  // per-unit key-window stride of the sort scratch
 constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
+constexpr int KEY_T = 256;        // cells per block of the per-cell sort kernels
 constexpr int NQ = 5;             // deposit quantities per bin: jy_lo, jy_hi, jz_lo, jz_hi, jx
 constexpr int WAIT_LIMIT = 1 << 22;  // bounded spin on an mbarrier before reporting a timeout
 
@@ -44,30 +53,50 @@ struct DevSpecies {
 };
 
 struct UnitTable {
-    int32_t* species;  // [max_units]
-    int32_t* start;    // first particle index
+    int32_t* run;      // [max_units] run of the unit
+    int32_t* species;  // species of the unit
+    int32_t* start;    // first particle index (in the run's arrays)
     int32_t* end;      // one past the last
     int32_t* lo;       // cell of the first particle at the last sort
     int32_t* hi;       // cell of the last particle at the last sort
-    int32_t* count;    // [3]: total units, units of species 0, units of species 1
+    int32_t* count;    // [1]: total units
+};
+
+// One run of a batch, as the kernels see it.
+struct RunDev {
+    DevSpecies sp[2][2];   // [species][particle buffer]
+    int32_t n[2];          // particles per species
+    float qm[2];           // charge / mass
+    float qw[2];           // charge * weight
+    float rad_w[2];        // weight * dx * mass (energy per unit gamma)
+    float lscale[2];       // 32-bit fixed-point scale of a warp deposit record (power of two)
+    int32_t lshift[2];     // shift from warp records to accumulator units
+    int32_t rr;            // radiation reaction on electrons
+    int32_t active;        // stepped by the batch
+    int32_t Nx, is, glen;
+    int32_t fpar;          // field / current buffer at batch step g: (g + fpar) & 1
+    float fp_inv;          // 2^-fp of the current accumulators
+    float* F[2][5];        // [buffer][Ex, Ey, Ez, By, Bz], padded
+    unsigned long long* J[2][3];  // [parity][Jx, Jy, Jz], padded
+    float* Jf[3];          // float J of the last step (read-back)
+    double* tally;         // [4]: radiated, flux in, flux out, spare
+    int32_t* keycount[2];  // sort scratch per species: [Nx + 2]
+    int32_t* keystart[2];  // [Nx + 2]; keystart[Nx] = particles
+    int32_t* blocksum[2];  // [Nx / 256 + 2]
+    int32_t* blockstart[2];
+    int32_t* tile_n[2];    // [Nx / TILE + 3]
+    int32_t* tile_first[2];
 };
 
 struct PushParams {
-    DevSpecies sp[2];
-    float qm[2];        // charge / mass
-    float qw[2];        // charge * weight
-    float rad_w[2];     // weight * dx * mass (energy per unit gamma)
-    int rr[2];          // radiation reaction on this species
-    const float* F[5];  // Ex, Ey, Ez, By, Bz, each pointing at element 0 of the padded array
-    unsigned long long* J[3];  // Jx, Jy, Jz accumulators (padded)
+    const RunDev* runs;
     UnitTable units;
     double* rad_part;   // [max_units] radiated energy of each unit since the last flush
     int* status;
-    int Nx;
+    int64_t gstep;      // batch step
     int k;              // steps since the last sort
+    int cur;            // particle buffer
     float cfl, dt, eps;
-    float lscale[2];    // per-species 32-bit fixed-point scale of a warp record (power of two)
-    int lshift[2];      // fp - log2(lscale): shift from warp records to accumulator units
 };
 
 struct LaserParams {
@@ -76,21 +105,16 @@ struct LaserParams {
 };
 
 struct FieldParams {
-    const float* Fo[5];  // fields at time n (padded)
-    float* Fn[5];        // fields at time n+1 (padded)
-    const unsigned long long* Jacc[3];  // this step's accumulators
-    unsigned long long* Jnext[3];       // zeroed for the next step
-    float* Jf[3];        // float J of this step (read-back)
-    double* tally;       // [0] radiated, [1] flux in, [2] flux out
-    int Nx, is;
-    int glen;            // length of every padded grid array
-    int64_t n;           // step index (t_n = n dt)
-    double dt, dx;
-    float c, hc, fdt;    // cfl, cfl/2, dt
-    float fp_inv;        // 2^-fp
-    // incident field (ay, az) at retarded times t_n (source node), t_n + dt/2 + dx/2
-    // (half node before it) and t_{n+1}: Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az
-    float inc[6];
+    const RunDev* runs;
+    const int32_t* blk_run;  // [blocks] run of each block
+    const int32_t* blk_i0;   // [blocks] first node of each block
+    // per run: incident field (ay, az) at retarded times t_n (source node),
+    // t_n + dt/2 + dx/2 (half node before it) and t_{n+1}:
+    // Ey_inc = Bz_inc = ay, Ez_inc = -By_inc = az
+    const float* inc;        // [runs * 6]
+    int64_t gstep;
+    double dt;
+    float c, hc, fdt;        // cfl, cfl/2, dt
 };
 
 // ---------------------------------------------------------------------------
@@ -149,27 +173,24 @@ void launch_push(const PushParams& P, int grid, cudaStream_t st);
 void launch_field(const FieldParams& P, int grid, cudaStream_t st);
 
 struct SortParams {
-    DevSpecies src[2], dst[2];
-    int64_t n[2];          // particle count per species
+    RunDev* runs;
+    int nruns;
     UnitTable units;
     int32_t* cnt;          // [max_units * SSTR] key counts per unit window
     int32_t* offs;         // [max_units * SSTR] destinations per unit window
-    int32_t* esc_cnt;      // [max_units]
-    int32_t* esc_off;      // [max_units]
-    int32_t* keycount[2];  // [Nx + 2]
-    int32_t* keystart[2];  // [Nx + 2]; keystart[Nx] = active count
-    int32_t* meta;         // [8]: [0..1] active particles at the last sort, [2..3] escapes since,
-                           // [4] error bits of the sort
-    int32_t* blocksum[2];  // [Nx/256 + 1] key counts per block of 256 cells
-    int32_t* blockstart[2];
-    int32_t* tile_n[2];    // [Nx/TILE + 1] units per tile
-    int32_t* tile_first[2];  // [Nx/TILE + 2] first unit of each tile
-    int Nx, k, max_units;
+    int32_t* rs_units;     // [4 * nruns]: units per (run, species) pair, then the first unit of each pair
+    int* status;
+    int k, cur, max_units;
+    int kb_max;            // key blocks of the largest run: ceil(max Nx / 256)
 };
-// Full re-sort of both species (bounded displacement since the last sort).
-void launch_sort(const SortParams& S, int n_unit_blocks, cudaStream_t st, int* launches);
-// Unit table from already sorted particles (after loading).
-void launch_build_units_from_sorted(const SortParams& S, cudaStream_t st, int* launches);
+// Full re-sort of every active run (bounded displacement since the last sort)
+// and the new unit table; particles move from buffer cur to 1 - cur.
+void launch_sort(const SortParams& S, cudaStream_t st, int* launches);
+// Unit table of every active run from its current, already sorted particles.
+void launch_build_units(const SortParams& S, cudaStream_t st, int* launches);
+// Add each run's per-unit radiated energy into its tally[0]; zero them.
+// rs_units as in SortParams.
+void launch_rad_flush(const RunDev* runs, int nruns, const int32_t* rs_units, double* rad_part, cudaStream_t st);
 
 void launch_foil(DevSpecies e, DevSpecies ion, int c0, int ncell, int ppc, uint64_t seed, cudaStream_t st);
 void launch_iota(int32_t* id, int64_t n, cudaStream_t st);
@@ -189,8 +210,6 @@ struct DiagParams {
 int launch_field_energy(const DiagParams& D, double* partials, int max_blocks, cudaStream_t st);
 int launch_kinetic(DevSpecies sp, int64_t n, double* partials, int max_blocks, cudaStream_t st);
 void launch_reduce_partials(const double* partials, int n, double scale, double* out, cudaStream_t st);
-// tally[0] += sum of rad_part[0 .. units.count[0]) in a fixed order; zero them.
-void launch_rad_flush(double* rad_part, const int32_t* unit_count, double* tally, cudaStream_t st);
 void launch_spectrum(DevSpecies sp, int64_t n, double mass_mev, int nbins, double e_min, double e_max,
                      unsigned long long* bins, cudaStream_t st);
 
