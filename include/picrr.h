@@ -177,10 +177,14 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the handle */
     int32_t n_units;          /* current work units (sorted particle chunks) */
     int32_t fp_bits;          /* fixed-point fraction bits of the current accumulators */
+    int64_t graph_launches;   /* CUDA-graph launches, each one sort interval of steps */
 } pic_stats_t;
 
 /* Counters and, when timing is on, CUDA-event times of each kernel class,
- * recorded on the launching stream. */
+ * recorded on the launching stream.  With timing off, every whole sort
+ * interval of steps that no run ends inside is launched as one captured CUDA
+ * graph (its pushes, Yee updates and the sort); with timing on, every kernel
+ * is launched on its own so that it can be timed. */
 pic_status pic_stats(pic_sim* sim, pic_stats_t* out);
 pic_status pic_set_timing(pic_sim* sim, int on);
 

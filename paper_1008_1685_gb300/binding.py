@@ -100,6 +100,7 @@ class Stats(C.Structure):
         ("device_bytes", C.c_int64),
         ("n_units", C.c_int32),
         ("fp_bits", C.c_int32),
+        ("graph_launches", C.c_int64),
     ]
 
     def as_dict(self):

@@ -13,13 +13,15 @@
 //      search; the per-cell totals are scanned into the new cell starts, and
 //      every (unit, cell) pair gets its destination offset in unit order;
 //   3. each unit scatters its particles, ranking equal cells in index order
-//      (warp match + per-warp counts combined in warp order), so the result
-//      does not depend on scheduling;
+//      (each warp owns a contiguous slice; warp match ranks within a warp and
+//      per-warp counts combined in warp order), so the result does not depend
+//      on scheduling;
 //   4. the unit table is rebuilt from the sorted cells: tiles of TILE cells,
 //      split into chunks of at most UNIT_P particles.
 // Every particle is read once and written once; the cell array is read once
 // more for the counts.
 #include <algorithm>
+#include <climits>
 
 #include "picrr_internal.cuh"
 
@@ -49,19 +51,28 @@ __global__ void __launch_bounds__(SORT_T) k_sort_count(const SortParams S) {
     __syncthreads();
     const int32_t* cell = R.sp[s][S.cur].cell;
     const int lane = threadIdx.x & 31;
-    for (int i0 = start; i0 < end; i0 += SORT_T) {  // block-uniform trip count
-        const int i = i0 + threadIdx.x;
-        int l = -1;
-        if (i < end) {
-            l = key_of(cell[i]) - wb;
-            if (!(l >= 0 && l < L && l < SSTR)) {
-                atomicOr(S.status, ST_WINDOW);
-                l = -1;
-            }
+    constexpr int U = 4;  // loads in flight per thread
+    for (int i0 = start; i0 < end; i0 += U * SORT_T) {  // block-uniform trip count
+        int c[U];
+#pragma unroll
+        for (int m = 0; m < U; ++m) {
+            const int i = i0 + m * SORT_T + threadIdx.x;
+            c[m] = i < end ? cell[i] : INT32_MIN;
         }
-        // lanes with the same cell add their count once
-        const unsigned peers = __match_any_sync(FULL, l);
-        if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[l], __popc(peers));
+#pragma unroll
+        for (int m = 0; m < U; ++m) {
+            int l = -1;
+            if (c[m] != INT32_MIN) {
+                l = key_of(c[m]) - wb;
+                if (!(l >= 0 && l < L && l < SSTR)) {
+                    atomicOr(S.status, ST_WINDOW);
+                    l = -1;
+                }
+            }
+            // lanes with the same cell add their count once
+            const unsigned peers = __match_any_sync(FULL, l);
+            if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[l], __popc(peers));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < SSTR; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = cnt[i];
@@ -217,19 +228,26 @@ __global__ void __launch_bounds__(KEY_T) k_sort_offsets(const SortParams S) {
     }
 }
 
-__device__ __forceinline__ void copy_particle(const DevSpecies& a, const DevSpecies& b, int i, int d) {
-    b.cell[d] = a.cell[i];
-    b.off[d] = a.off[i];
-    b.px[d] = a.px[i];
-    b.py[d] = a.py[i];
-    b.pz[d] = a.pz[i];
-    b.id[d] = a.id[i];
-}
 
 // ---- 3. stable scatter ----------------------------------------------------------
+// Each warp owns one contiguous slice of the unit's particles.  Pass 1 counts
+// the slice's particles per cell (warp match; only the warp writes its row);
+// the rows are then turned into per-warp destination starts (unit offset plus
+// the counts of the warps before, in warp order); pass 2 walks the slice
+// again in order and places each particle at its warp's running start plus
+// its rank among the lanes with the same cell.  Equal cells therefore keep
+// index order, with two block barriers per unit.
+constexpr int SC_W = SORT_T / 32;
+constexpr int SC_U = 4;  // slice rows of 32 particles in flight per pass step
+
+__device__ __forceinline__ int window_key(const int32_t* cell, int i, int we, int wb) {
+    if (i >= we) return -1;
+    const int l = key_of(cell[i]) - wb;
+    return (l >= 0 && l < SSTR) ? l : -1;  // out of window cannot happen (counted as an error)
+}
+
 __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
-    __shared__ int base[SSTR];
-    __shared__ int wcnt[SORT_T / 32][SSTR];
+    __shared__ int row[SC_W][SSTR];
     const int u = blockIdx.x;
     if (u >= S.units.count[0]) return;
     const RunDev& R = S.runs[S.units.run[u]];
@@ -240,35 +258,73 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
     const int wb = S.units.lo[u] - S.k;
     const DevSpecies src = R.sp[s][S.cur];
     const DevSpecies dst = R.sp[s][1 - S.cur];
-    for (int i = tid; i < SSTR; i += SORT_T) base[i] = 0;
-    for (int i = tid; i < (SORT_T / 32) * SSTR; i += SORT_T) (&wcnt[0][0])[i] = 0;
+    const int per = (end - start + SC_W - 1) / SC_W;
+    const int ws = min(end, start + warp * per), we = min(end, ws + per);
+    for (int i = tid; i < SC_W * SSTR; i += SORT_T) (&row[0][0])[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    for (int c0 = start; c0 < end; c0 += SORT_T) {
-        const int i = c0 + tid;
-        int key = -1;
-        if (i < end) {
-            const int l = key_of(src.cell[i]) - wb;
-            key = (l >= 0 && l < SSTR) ? l : -1;  // out of window cannot happen (counted as an error)
+    // pass 1: this warp's counts per cell
+    for (int i0 = ws; i0 < we; i0 += 32 * SC_U) {  // warp-uniform
+        int key[SC_U];
+#pragma unroll
+        for (int m = 0; m < SC_U; ++m) key[m] = window_key(src.cell, i0 + 32 * m + lane, we, wb);
+#pragma unroll
+        for (int m = 0; m < SC_U; ++m) {
+            const unsigned peers = __match_any_sync(FULL, key[m]);
+            if (key[m] >= 0 && lane == __ffs(peers) - 1) row[warp][key[m]] += __popc(peers);
+            __syncwarp();
         }
-        const unsigned peers = __match_any_sync(FULL, key);
-        const int rw = __popc(peers & lt);
-        const bool leader = (__ffs(peers) - 1) == lane;
-        if (leader && key >= 0) wcnt[warp][key] = __popc(peers);
-        __syncthreads();
-        int dest = -1;
-        if (key >= 0) {
-            int r = base[key] + rw;
-            for (int w = 0; w < warp; ++w) r += wcnt[w][key];
-            dest = S.offs[static_cast<size_t>(u) * SSTR + key] + r;
+    }
+    __syncthreads();
+    // per cell: destination start of each warp's particles, in warp order
+    for (int l = tid; l < SSTR; l += SORT_T) {
+        int run = S.offs[static_cast<size_t>(u) * SSTR + l];
+#pragma unroll
+        for (int w = 0; w < SC_W; ++w) {
+            const int c = row[w][l];
+            row[w][l] = run;
+            run += c;
         }
-        __syncthreads();
-        if (leader && key >= 0) {
-            atomicAdd(&base[key], __popc(peers));
-            wcnt[warp][key] = 0;
+    }
+    __syncthreads();
+    // pass 2: place the slice's particles in order
+    for (int i0 = ws; i0 < we; i0 += 32 * SC_U) {  // warp-uniform
+        int cl[SC_U], id[SC_U];
+        float of[SC_U], x[SC_U], y[SC_U], z[SC_U];
+#pragma unroll
+        for (int m = 0; m < SC_U; ++m) {
+            const int i = i0 + 32 * m + lane;
+            if (i < we) {
+                cl[m] = src.cell[i];
+                of[m] = src.off[i];
+                x[m] = src.px[i];
+                y[m] = src.py[i];
+                z[m] = src.pz[i];
+                id[m] = src.id[i];
+            }
         }
-        __syncthreads();
-        if (dest >= 0) copy_particle(src, dst, i, dest);
+#pragma unroll
+        for (int m = 0; m < SC_U; ++m) {
+            const int i = i0 + 32 * m + lane;
+            int key = -1;
+            if (i < we) {
+                const int l = key_of(cl[m]) - wb;
+                key = (l >= 0 && l < SSTR) ? l : -1;
+            }
+            const unsigned peers = __match_any_sync(FULL, key);
+            const int d = key >= 0 ? row[warp][key] + __popc(peers & lt) : -1;
+            __syncwarp();
+            if (key >= 0 && lane == __ffs(peers) - 1) row[warp][key] += __popc(peers);
+            __syncwarp();
+            if (d >= 0) {
+                dst.cell[d] = cl[m];
+                dst.off[d] = of[m];
+                dst.px[d] = x[m];
+                dst.py[d] = y[m];
+                dst.pz[d] = z[m];
+                dst.id[d] = id[m];
+            }
+        }
     }
 }
 

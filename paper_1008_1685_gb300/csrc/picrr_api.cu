@@ -30,7 +30,7 @@ constexpr double kMec2MeV = 0.51099895000;  // electron rest energy, MeV
 constexpr double kMpMe = 1836.15267343;     // proton mass / electron mass
 constexpr double kMuMe = 1822.888486209;    // atomic mass unit / electron mass
 constexpr int kMaxDiagBlocks = 1024;
-constexpr int kIncRing = 64;                // slots of the per-step laser-source upload ring
+constexpr int kIncRing = 16;                // slots of the laser-source upload ring (one chunk of steps each)
 
 thread_local std::string g_null_error;  // failures of calls without a handle
 
@@ -125,10 +125,21 @@ struct Batch {
     int32_t* d_blk_run = nullptr;
     int32_t* d_blk_i0 = nullptr;
     int nblk = 0, blk_cap = 0;
-    float* d_inc = nullptr;
-    float* h_inc = nullptr;  // pinned ring [kIncRing][max_runs * 6]
+    float* d_inc = nullptr;  // [sort_interval][max_runs * 6]
+    float* h_inc = nullptr;  // pinned ring [kIncRing][sort_interval][max_runs * 6]
     cudaEvent_t inc_ev[kIncRing] = {};
     int inc_slot = 0;
+
+    // CUDA graphs of one sort interval of steps (its pushes, Yee updates and
+    // the sort that ends it), by [step parity at the chunk start][current
+    // particle buffer].  The kernels read the run table at run time, so a
+    // graph stays valid while launch shapes and table pointers do (epoch).
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2][2] = {};
+    uint64_t graph_epoch[2][2] = {};
+    uint64_t epoch = 1;
+    bool graphs_on = true;
+    int64_t graph_launches = 0;
 
     UnitTable units{};
     int max_units = 0;
@@ -333,7 +344,7 @@ pic_status batch_create(const pic_config* cfg, int max_runs, Batch** out) {
     }
     b->stream = b->own_stream;
     if ((st = dalloc_t(b, b->mem, &b->d_runs, static_cast<size_t>(max_runs))) != PIC_OK ||
-        (st = dalloc_t(b, b->mem, &b->d_inc, static_cast<size_t>(max_runs) * 6)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->d_inc, static_cast<size_t>(max_runs) * 6 * b->sort_interval)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->d_status, 4)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->diag_partials, kMaxDiagBlocks)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->diag_out, 8)) != PIC_OK ||
@@ -343,13 +354,18 @@ pic_status batch_create(const pic_config* cfg, int max_runs, Batch** out) {
         return st;
     }
     if (cudaMallocHost(&b->h_runs, sizeof(RunDev) * max_runs) != cudaSuccess ||
-        cudaMallocHost(&b->h_inc, sizeof(float) * 6 * max_runs * kIncRing) != cudaSuccess) {
+        cudaMallocHost(&b->h_inc, sizeof(float) * 6 * max_runs * b->sort_interval * kIncRing) != cudaSuccess) {
         cudaGetLastError();
         batch_destroy(b);
         return fail(nullptr, PIC_ERR_OOM, "pinned host allocation failed");
     }
     std::memset(b->h_runs, 0, sizeof(RunDev) * max_runs);
     for (int i = 0; i < kIncRing; ++i) cudaEventCreateWithFlags(&b->inc_ev[i], cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        batch_destroy(b);
+        return fail(nullptr, PIC_ERR_CUDA, "cudaStreamCreate failed");
+    }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         batch_destroy(b);
@@ -375,6 +391,10 @@ void batch_destroy(Batch* b) {
         if (b->inc_ev[i]) cudaEventDestroy(b->inc_ev[i]);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->h_inc) cudaFreeHost(b->h_inc);
+    for (auto& row : b->graph)
+        for (auto& g : row)
+            if (g) cudaGraphExecDestroy(g);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
 }
@@ -733,6 +753,7 @@ pic_status ensure_units(Batch* b, int need) {
     b->cnt = cn;
     b->offs = of;
     b->max_units = mu;
+    b->epoch++;
     return PIC_OK;
 }
 
@@ -811,14 +832,16 @@ pic_status upload_blocks(Batch* b) {
     }
     b->nblk = n;
     b->layout_dirty = false;
+    b->epoch++;  // the Yee grid, and possibly the sort's, changed shape
     return PIC_OK;
 }
 
-void rad_flush(Batch* b) {
+void rad_flush(Batch* b, cudaStream_t st) {
     if (b->max_units == 0) return;
-    launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, b->stream);
+    launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, st);
     b->launches++;
 }
+void rad_flush(Batch* b) { rad_flush(b, b->stream); }
 
 void do_sort(Batch* b) {
     SortParams S = sort_params(b);
@@ -896,24 +919,92 @@ void deactivate(Batch* b, int id) {
     b->table_dirty = b->layout_dirty = true;
 }
 
-// Laser source values of the coming step for every active run, uploaded
-// through a pinned ring.
-pic_status upload_incident(Batch* b) {
-    float* h = b->h_inc + static_cast<size_t>(b->inc_slot) * 6 * b->max_runs;
+// Laser source values of the coming `steps` steps for every active run,
+// uploaded through a pinned ring: step j of the chunk reads d_inc + j * 6 * max_runs.
+pic_status upload_incident(Batch* b, int steps) {
+    const size_t per_step = static_cast<size_t>(6) * b->max_runs;
+    float* h = b->h_inc + static_cast<size_t>(b->inc_slot) * per_step * b->sort_interval;
     PIC_CK(b, cudaEventSynchronize(b->inc_ev[b->inc_slot]));
-    int hi = -1;
-    for (int i = 0; i < b->max_runs; ++i) {
-        const RunHost& r = b->runs[i];
-        if (!r.used || !r.active) continue;
-        hi = i;
-        const double tn = static_cast<double>(b->gstep - r.admit_step) * b->dt;
-        const double ts[3] = {tn, tn + 0.5 * b->dt + 0.5 * b->dx, tn + b->dt};
-        for (int k = 0; k < 3; ++k) incident(r.laser, ts[k], &h[6 * i + 2 * k], &h[6 * i + 2 * k + 1]);
+    for (int j = 0; j < steps; ++j) {
+        float* hj = h + j * per_step;
+        for (int i = 0; i < b->max_runs; ++i) {
+            const RunHost& r = b->runs[i];
+            if (!r.used || !r.active) continue;
+            const double tn = static_cast<double>(b->gstep + j - r.admit_step) * b->dt;
+            const double ts[3] = {tn, tn + 0.5 * b->dt + 0.5 * b->dx, tn + b->dt};
+            for (int k = 0; k < 3; ++k) incident(r.laser, ts[k], &hj[6 * i + 2 * k], &hj[6 * i + 2 * k + 1]);
+        }
     }
-    if (hi >= 0)
-        PIC_CK(b, cudaMemcpyAsync(b->d_inc, h, sizeof(float) * 6 * (hi + 1), cudaMemcpyHostToDevice, b->stream));
+    PIC_CK(b, cudaMemcpyAsync(b->d_inc, h, sizeof(float) * per_step * steps, cudaMemcpyHostToDevice, b->stream));
     cudaEventRecord(b->inc_ev[b->inc_slot], b->stream);
     b->inc_slot = (b->inc_slot + 1) % kIncRing;
+    return PIC_OK;
+}
+
+PushParams push_params(const Batch* b, int64_t gstep, int k, int cur) {
+    PushParams P{};
+    P.runs = b->d_runs;
+    P.units = b->units;
+    P.rad_part = b->rad_part;
+    P.status = b->d_status;
+    P.gstep = gstep;
+    P.k = k;
+    P.cur = cur;
+    P.cfl = static_cast<float>(b->cfl);
+    P.dt = static_cast<float>(b->dt);
+    P.eps = static_cast<float>(b->eps);
+    return P;
+}
+
+FieldParams field_params(const Batch* b, int64_t gstep, int j) {
+    FieldParams Q{};
+    Q.runs = b->d_runs;
+    Q.blk_run = b->d_blk_run;
+    Q.blk_i0 = b->d_blk_i0;
+    Q.inc = b->d_inc + static_cast<size_t>(j) * 6 * b->max_runs;
+    Q.gstep = gstep;
+    Q.dt = b->dt;
+    Q.c = static_cast<float>(b->cfl);
+    Q.hc = static_cast<float>(0.5 * b->cfl);
+    Q.fdt = static_cast<float>(b->dt);
+    return Q;
+}
+
+// The graph of one sort interval starting at step parity par0 with current
+// particle buffer cur (captured on the batch's capture stream, then reused).
+pic_status chunk_graph(Batch* b, int par0, int cur, cudaGraphExec_t* out) {
+    cudaGraphExec_t& ex = b->graph[par0][cur];
+    if (ex && b->graph_epoch[par0][cur] == b->epoch) {
+        *out = ex;
+        return PIC_OK;
+    }
+    if (ex) {
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+    }
+    const int I = b->sort_interval;
+    cudaStream_t cs = b->cap_stream;
+    PIC_CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < I; ++j) {
+        launch_push(push_params(b, par0 + j, j, cur), b->max_units, cs);
+        launch_field(field_params(b, par0 + j, j), b->nblk, cs);
+    }
+    launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, cs);
+    SortParams S = sort_params(b);
+    S.k = I;
+    S.cur = cur;
+    int nl = 0;
+    launch_sort(S, cs, &nl);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ex = nullptr;
+        return cuda_fail(b, e, "chunk graph");
+    }
+    b->graph_epoch[par0][cur] = b->epoch;
+    *out = ex;
     return PIC_OK;
 }
 
@@ -923,40 +1014,56 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
     if (st != PIC_OK) return st;
     if ((st = upload_table(b)) != PIC_OK) return st;
     if ((st = upload_blocks(b)) != PIC_OK) return st;
+    const int I = b->sort_interval;
     int64_t it = 0;
-    for (; it < n; ++it) {
+    while (it < n) {
         int nact = 0;
-        for (auto& r : b->runs) nact += (r.used && r.active) ? 1 : 0;
+        bool whole_chunk = b->graphs_on && !b->timing && b->since_sort == 0 && n - it >= I;
+        for (auto& r : b->runs) {
+            if (!r.used || !r.active) continue;
+            nact++;
+            if (r.steps_target > 0 && r.steps_target - r.steps_done < I) whole_chunk = false;
+        }
         if (nact == 0) break;
-        if ((st = upload_incident(b)) != PIC_OK) return st;
-        PushParams P{};
-        P.runs = b->d_runs;
-        P.units = b->units;
-        P.rad_part = b->rad_part;
-        P.status = b->d_status;
-        P.gstep = b->gstep;
-        P.k = b->since_sort;
-        P.cur = b->cur;
-        P.cfl = static_cast<float>(b->cfl);
-        P.dt = static_cast<float>(b->dt);
-        P.eps = static_cast<float>(b->eps);
-        FieldParams Q{};
-        Q.runs = b->d_runs;
-        Q.blk_run = b->d_blk_run;
-        Q.blk_i0 = b->d_blk_i0;
-        Q.inc = b->d_inc;
-        Q.gstep = b->gstep;
-        Q.dt = b->dt;
-        Q.c = static_cast<float>(b->cfl);
-        Q.hc = static_cast<float>(0.5 * b->cfl);
-        Q.fdt = static_cast<float>(b->dt);
+        if (whole_chunk) {
+            // a whole sort interval as one graph launch; no run ends before its last step
+            cudaGraphExec_t ex = nullptr;
+            if ((st = chunk_graph(b, static_cast<int>(b->gstep & 1), b->cur, &ex)) != PIC_OK) return st;
+            if ((st = upload_incident(b, I)) != PIC_OK) return st;
+            PIC_CK(b, cudaGraphLaunch(ex, b->stream));
+            b->graph_launches++;
+            b->launches += 2 * I + 1 + 8;
+            b->push_launches += I;
+            b->gstep += I;
+            b->cur ^= 1;
+            b->sorts++;
+            it += I;
+            bool ended = false;
+            for (auto& r : b->runs) {
+                if (!r.used || !r.active) continue;
+                r.steps_done += I;
+                if (r.steps_target > 0 && r.steps_done >= r.steps_target) ended = true;
+            }
+            if (ended) {  // runs that end with this chunk: sorted and flushed by it
+                for (int i = 0; i < b->max_runs; ++i) {
+                    RunHost& r = b->runs[i];
+                    if (r.used && r.active && r.steps_target > 0 && r.steps_done >= r.steps_target) deactivate(b, i);
+                }
+                if ((st = upload_table(b)) != PIC_OK) return st;
+                if ((st = upload_blocks(b)) != PIC_OK) return st;
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(b, e, "chunk launch");
+            continue;
+        }
+        if ((st = upload_incident(b, 1)) != PIC_OK) return st;
         {
             Timed t(b, 0);
-            launch_push(P, b->max_units, b->stream);
+            launch_push(push_params(b, b->gstep, b->since_sort, b->cur), b->max_units, b->stream);
         }
         {
             Timed t(b, 1);
-            launch_field(Q, b->nblk, b->stream);
+            launch_field(field_params(b, b->gstep, 0), b->nblk, b->stream);
         }
         b->launches += 2;
         b->push_launches++;
@@ -968,8 +1075,10 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
             r.steps_done++;
             if (r.steps_target > 0 && r.steps_done >= r.steps_target) ended = true;
         }
+        // a run that ends on a sort step is sorted first, as it would be alone
+        if (b->since_sort >= b->sort_interval) do_sort(b);
         if (ended) {
-            rad_flush(b);  // finished runs take their radiated energy with them
+            if (b->since_sort > 0) rad_flush(b);  // finished runs take their radiated energy with them
             for (int i = 0; i < b->max_runs; ++i) {
                 RunHost& r = b->runs[i];
                 if (r.used && r.active && r.steps_target > 0 && r.steps_done >= r.steps_target) deactivate(b, i);
@@ -977,11 +1086,11 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
             if ((st = upload_table(b)) != PIC_OK) return st;
             if ((st = upload_blocks(b)) != PIC_OK) return st;
         }
-        if (b->since_sort >= b->sort_interval) do_sort(b);
         if ((it & 255) == 255) {
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(b, e, "step launch");
         }
+        ++it;
     }
     if (it > 0 && b->since_sort > 0) rad_flush(b);
     cudaError_t e = cudaStreamSynchronize(b->stream);
@@ -1147,6 +1256,7 @@ void fill_stats(Batch* b, pic_stats_t* out) {
     out->field_ms = b->field_ms;
     out->sort_ms = b->sort_ms;
     out->timed_push_launches = b->timed_push;
+    out->graph_launches = b->graph_launches;
     out->device_bytes = static_cast<int64_t>(b->bytes);
     int64_t act = 0;
     int fp = 0;

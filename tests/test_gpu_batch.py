@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 CPL = 100
 RUNS = [
     dict(length_lambda=8, foil_x0=3.0, foil_thickness=0.5, ne=40.0, a0=150.0, polarization=0, duration=3.0,
-         steps=700, rr_on=True, ppc=24, seed=5),
+         steps=704, rr_on=True, ppc=24, seed=5),
     dict(length_lambda=12, foil_x0=4.0, foil_thickness=1.0, ne=90.0, a0=300.0, polarization=1, duration=4.0,
          steps=1000, rr_on=False, ppc=48, seed=6),
     dict(length_lambda=6, foil_x0=2.0, foil_thickness=0.3, ne=120.0, a0=500.0, polarization=0, duration=2.0,
@@ -186,3 +186,24 @@ def test_batch_argument_errors(picrr):
     assert b.step(100) == 45
     b.release_run(rid)
     b.close()
+
+
+def test_graph_chunks_equal_single_launches(picrr):
+    """With timing off, whole sort intervals run as one captured CUDA graph;
+    with timing on, every kernel is launched on its own.  Same results."""
+    d = RUNS[0]
+    out, st = [], []
+    for timing in (False, True):
+        g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
+                      seed=d["seed"])
+        g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
+        g.set_timing(timing)
+        for n in (5, 3, 200, d["steps"] - 208):  # chunks start only on sort boundaries
+            g.step(n)
+        out.append(snapshot(g.particles, g.field, g.energy, g.spectra))
+        st.append(g.stats())
+        g.close()
+    assert st[0]["graph_launches"] == (d["steps"] - 8) // 8 and st[1]["graph_launches"] == 0
+    assert st[0]["kernel_launches"] == st[1]["kernel_launches"]
+    assert_same(out[0], out[1], "graph vs single launches")
