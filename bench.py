@@ -71,7 +71,8 @@ def desc_particles(d, cpl):
 # the served request stream: Poisson arrivals, sizes log-uniform in 1e4..1e6
 # particles per species, 20..200 periods, physical parameters as in the scan,
 # admission by device memory under a 150 GB budget
-SERVE = dict(rate=20.0, window_s=10.0, cap_s=45.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77)
+SERVE = dict(rate=20.0, window_s=10.0, cap_s=45.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77,
+             policy="sjf", resident=24_000_000)
 
 
 def serve_requests(rate, window_s, seed, w=SCAN):
@@ -116,6 +117,7 @@ def serve_leg(picrr, device, cfg=SERVE, w=SCAN):
     reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
     srv = picrr.Server(w["cells_per_lambda"], max_runs=cfg["max_runs"], chunk_steps=cfg["chunk"], cfl=w["cfl"],
                        sort_interval=w["sort_interval"], device=device, hbm_budget_bytes=cfg["budget"])
+    srv.set_policy(picrr.SERVE_SHORTEST_FIRST if cfg["policy"] == "sjf" else picrr.SERVE_FIFO, cfg["resident"])
     tickets = []
     t0 = time.perf_counter()
 
@@ -153,16 +155,21 @@ def serve_leg(picrr, device, cfg=SERVE, w=SCAN):
 
 
 def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
-    """The same request stream served one run at a time in arrival order
-    through the single-run API (no batching), under the same time cap."""
+    """The same request stream served one run at a time through the
+    single-run API (no batching), under the same time cap and the same order
+    policy (arrival order, or the least work among the arrived requests)."""
     reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    work = [desc_particles(d, w["cells_per_lambda"]) * d["steps"] for _, d in reqs]
     t0 = time.perf_counter()
-    lat, i = [], 0
-    while i < len(reqs) and time.perf_counter() - t0 < cfg["cap_s"]:
-        ta, d = reqs[i]
-        dt = t0 + ta - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
+    lat, pending = [], list(range(len(reqs)))
+    while pending and time.perf_counter() - t0 < cfg["cap_s"]:
+        now = time.perf_counter() - t0
+        arrived = [j for j in pending if reqs[j][0] <= now]
+        if not arrived:
+            time.sleep(max(0.0, reqs[pending[0]][0] - now))
+            continue
+        j = min(arrived, key=lambda q: (work[q], q)) if cfg["policy"] == "sjf" else arrived[0]
+        ta, d = reqs[j]
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
                       sort_interval=w["sort_interval"], seed=d["seed"], device=device)
         s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
@@ -175,11 +182,10 @@ def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
             s.spectra(0, 200, 0.0, 2000.0)
             s.energy()
             lat.append(time.perf_counter() - t0 - ta)
-            i += 1
+            pending.remove(j)
         s.close()
     el = time.perf_counter() - t0
-    arrived = [ta for ta, _ in reqs[i:] if ta <= el]
-    return _latency_summary(lat, [el - ta for ta in arrived], el, len(reqs))
+    return _latency_summary(lat, [el - reqs[j][0] for j in pending if reqs[j][0] <= el], el, len(reqs))
 
 
 def batched_scan(picrr, device, n_runs, w=SCAN):
@@ -356,7 +362,7 @@ def host_foil(np, torch, w=LARGE):
     return host
 
 
-def e2e_run(picrr, torch, device, steps, host):
+def e2e_run(picrr, torch, device, steps, host, shapes=None):
     """Through the public C ABI with host buffers: create, upload the particles
     from pinned host memory, inject, step, read spectra + energy back."""
     w = LARGE
@@ -366,6 +372,8 @@ def e2e_run(picrr, torch, device, steps, host):
         c, o, x, y, z = host[sp]
         s.load_particles_f32(sp, c, o, x, y, z, *host["species"][sp])
     s.inject_laser(w["a0"], w["pol"], 0, w["duration"])
+    if shapes:
+        s.set_shapes(shapes["unit_particles"], shapes["sort_interval"])
     s.step(steps)
     counts, rad = s.spectra(1, 200, 0.0, 2000.0)
     en = s.energy()
@@ -386,6 +394,9 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=40)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no tuner run)")
+    ap.add_argument("--shapes", default=None,
+                    help="UNIT,INTERVAL: set these launch shapes instead of running the tuner (profiling)")
     ap.add_argument("--scan-runs", type=int, default=SCAN["n_runs"], help="runs of the batched scan (0: skip)")
     ap.add_argument("--plain-runs", type=int, default=8,
                     help="runs of the scan stepped one at a time for the plain comparison (0: skip)")
@@ -393,6 +404,10 @@ def main():
                     help="seconds of request arrivals of the serving leg (0: skip)")
     ap.add_argument("--serve-cap", type=float, default=SERVE["cap_s"], help="time cap of each serving arm (s)")
     ap.add_argument("--serve-rate", type=float, default=SERVE["rate"], help="request arrivals per second")
+    ap.add_argument("--serve-policy", default=SERVE["policy"], choices=["sjf", "fifo"],
+                    help="admission order of both serving arms: least work first, or arrival order")
+    ap.add_argument("--serve-resident", type=int, default=SERVE["resident"],
+                    help="particles stepping at once in the server (0: no cap)")
     ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
                     help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
@@ -417,9 +432,26 @@ def main():
     import paper_1008_1685_gb300 as picrr
 
     w = dict(LARGE, ppc=args.ppc)
+    shapes = None
+    if args.shapes:
+        u, k = (int(v) for v in args.shapes.split(","))
+        shapes = {"unit_particles": u, "sort_interval": k, "tuned": False}
+    elif not args.no_tune:
+        # launch shapes picked by the tuner on an identical run (its trial steps are
+        # real steps, so the measured run starts fresh)
+        t = make_sim(picrr, local)
+        t.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
+        t.inject_laser(w["a0"], w["pol"], 0, w["duration"])
+        unit, interval, tms = t.tune_shapes(64)
+        t.close()
+        shapes = {"unit_particles": unit, "sort_interval": interval, "tuned": True,
+                  "trial_ms_per_step": {"unit_2048_4096_8192_16384": [round(v, 4) for v in tms[:4]],
+                                        "interval_4_8_16_32": [round(v, 4) for v in tms[4:]]}}
     sim = make_sim(picrr, local)
     sim.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
     sim.inject_laser(w["a0"], w["pol"], 0, w["duration"])
+    if shapes:
+        sim.set_shapes(shapes["unit_particles"], shapes["sort_interval"])
     stream = torch.cuda.current_stream()
     sim.set_stream(stream.cuda_stream)
     sim.step(args.warmup)
@@ -455,11 +487,12 @@ def main():
     e2e = None
     if not args.no_e2e:
         host = host_foil(np, torch)
-        ev, h2d, d2h = e2e_run(picrr, torch, local, args.steps, host)
+        ev, h2d, d2h = e2e_run(picrr, torch, local, args.steps, host, shapes)
         e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps,
                "what": "pic_create + pic_load_particles_f32 from pinned host SoA + pic_inject_laser + "
-                       "pic_step_n(steps) + pic_spectra + pic_energy, host wall clock"}
+                       "pic_set_shapes (the tuned shapes) + pic_step_n(steps) + pic_spectra + pic_energy, "
+                       "host wall clock"}
 
     scan = None
     if args.scan_runs > 0:
@@ -476,15 +509,18 @@ def main():
 
     serving = None
     if args.serve_window > 0:
-        cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate)
+        cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
+                   policy=args.serve_policy, resident=args.serve_resident)
         serving = serve_leg(picrr, local, cfg)
         serving["plain"] = plain_serve_leg(picrr, local, cfg)
         serving["overloaded"] = serving["offered_particle_steps_per_s"] > serving["served_particle_steps_per_s"]
         serving["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
                                "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
-                               "the scan; 150 GB admission budget, %d slots, %d-step chunks; each arm capped at %g s; "
-                               "latency = submission to ion + electron spectra on the host"
-                               % (cfg["rate"], cfg["window_s"], cfg["seed"], cfg["max_runs"], cfg["chunk"],
+                               "the scan; 150 GB admission budget, %d slots, at most %d particles stepping at once, %d-step "
+                               "chunks, admission %s in both arms; each arm capped at %g s; latency = submission "
+                               "to ion + electron spectra on the host"
+                               % (cfg["rate"], cfg["window_s"], cfg["seed"], cfg["max_runs"], cfg["resident"],
+                                  cfg["chunk"], "least work first" if cfg["policy"] == "sjf" else "in arrival order",
                                   cfg["cap_s"]))
 
     cpu = None
@@ -500,7 +536,8 @@ def main():
             "config": {"workload": "large single run: 200,000 cells (100 lambda, lambda/2000), 2-lambda H foil "
                                    "n_e=100 n_c, 8000 ppc/species (32M e + 32M p), CP a0=500, RR on",
                        "particles": n_active, "particles_end": n_active_end, "cells": 200000,
-                       "sort_interval": w["sort_interval"],
+                       "sort_interval": shapes["sort_interval"] if shapes else w["sort_interval"],
+                       "shapes": shapes,
                        "l2": "inputs larger than L2: 2.56 GB particle state streamed per step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

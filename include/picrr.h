@@ -164,6 +164,23 @@ pic_status pic_read_particles(pic_sim* sim, int species, int64_t cap, double* x,
  * or Nx half-node values; *n (nullable) receives the count. */
 pic_status pic_read_fields(pic_sim* sim, int comp, int64_t cap, double* out, int64_t* n);
 
+/* Skin-layer snapshot of Sec. 4 (Figs. 2 and 4) for one species at the
+ * current step, computed on the device: per particle the friction
+ * coefficient d = eps gamma^2 [f_L^2 - (v.f_L)^2] of Eq. (damping) (the
+ * strength of the RR force in units of m omega c) and the quantum parameter
+ * chi = gamma sqrt(f_L^2 - (v.f_L)^2) / E_cr, E_cr = m c^2/(hbar omega) in
+ * field units (for a particle crossing a plane wave this is the
+ * gamma sqrt(I/I_cr) of the classical validity condition of Sec. 2; the
+ * classical treatment needs chi << 1).  Both are evaluated from the stored
+ * momentum p^{n-1/2} and the fields E^n, B^n interpolated at x^n as the push
+ * interpolates them; frozen particles give 0.  summary (nullable, [3]):
+ * max d, max chi, number of particles with chi >= chi_flag (chi_flag >= 0).
+ * With cap > 0, x (c/omega), p_x, p_perp = sqrt(p_y^2 + p_z^2), d and chi
+ * (each nullable) receive the values of the first cap particles in load
+ * order, as pic_read_particles.  *n (nullable) receives the species count. */
+pic_status pic_snapshot(pic_sim* sim, int species, double chi_flag, int64_t cap, double* x, double* px,
+                        double* pperp, double* d, double* chi, double* summary, int64_t* n);
+
 typedef struct {
     int64_t steps;            /* steps completed since creation */
     int64_t kernel_launches;  /* device kernels launched by this handle */
@@ -179,6 +196,27 @@ typedef struct {
     int32_t fp_bits;          /* fixed-point fraction bits of the current accumulators */
     int64_t graph_launches;   /* CUDA-graph launches, each one sort interval of steps */
 } pic_stats_t;
+
+/* Launch shapes.  unit_particles: the most particles one CTA of the fused
+ * push kernel takes (its work unit), a power of two in [1024, 16384]
+ * (default 4096); sort_interval in [1, 32].  Larger units amortise each
+ * CTA's fixed costs on dense foils; smaller ones keep the GPU busy when few
+ * particles are spread thinly.  A new unit size takes effect at once (the
+ * run is sorted if needed and its unit table rebuilt).  Both change only the
+ * order of single-precision sums. */
+pic_status pic_set_shapes(pic_sim* sim, int unit_particles, int sort_interval);
+
+/* Shape tuner.  Steps the run for a trial of about steps_per_candidate steps
+ * (rounded to whole sort intervals, after one warm-up interval) at each unit
+ * size of {2048, 4096, 8192, 16384} with the current sort interval, keeps
+ * the fastest, then at each sort interval of {4, 8, 16, 32}; measures the wall
+ * time per step (CUDA graphs, as pic_step_n runs them) and keeps the fastest
+ * pair.  *unit_particles and *sort_interval (nullable) receive it;
+ * ms_per_step[8] (nullable) the measured times per step (unit sizes, then
+ * intervals; -1 where not measured).  The trial steps are real steps of the
+ * run.  Timing must be off. */
+pic_status pic_tune_shapes(pic_sim* sim, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
+                           double* ms_per_step);
 
 /* Counters and, when timing is on, CUDA-event times of each kernel class,
  * recorded on the launching stream.  With timing off, every whole sort
@@ -223,7 +261,7 @@ typedef struct {
     int64_t steps;         /* the run stops after this many steps (>= 1) */
 } pic_run_desc;
 
-/* Batch with room for max_runs runs (1..65536) on common->device. */
+/* Batch with room for max_runs runs (1..8192) on common->device. */
 pic_status pic_batch_create(const pic_config* common, int max_runs, pic_batch** out);
 /* As pic_set_stream. */
 pic_status pic_batch_set_stream(pic_batch* batch, void* cuda_stream);
@@ -245,6 +283,9 @@ pic_status pic_batch_spectra(pic_batch* batch, int run, int species, int nbins, 
 pic_status pic_batch_read_particles(pic_batch* batch, int run, int species, int64_t cap, double* x,
                                     double* px, double* py, double* pz, int32_t* flag, int64_t* n);
 pic_status pic_batch_read_fields(pic_batch* batch, int run, int comp, int64_t cap, double* out, int64_t* n);
+/* As pic_snapshot, for one run of the batch. */
+pic_status pic_batch_snapshot(pic_batch* batch, int run, int species, double chi_flag, int64_t cap, double* x,
+                              double* px, double* pperp, double* d, double* chi, double* summary, int64_t* n);
 /* Free a finished run's device memory; its slot can take a new run. */
 pic_status pic_batch_release_run(pic_batch* batch, int run);
 /* Device bytes the run described by desc would take in this batch: its grid,
@@ -253,6 +294,10 @@ pic_status pic_batch_release_run(pic_batch* batch, int run);
  * admission by memory.  Reads only the batch's configuration, so it may be
  * called from any thread; its error message is pic_batch_last_error(NULL). */
 pic_status pic_batch_run_footprint(const pic_batch* batch, const pic_run_desc* desc, size_t* bytes);
+/* As pic_set_shapes / pic_tune_shapes, for all active runs of the batch together. */
+pic_status pic_batch_set_shapes(pic_batch* batch, int unit_particles, int sort_interval);
+pic_status pic_batch_tune_shapes(pic_batch* batch, int64_t steps_per_candidate, int* unit_particles,
+                                 int* sort_interval, double* ms_per_step);
 pic_status pic_batch_stats(pic_batch* batch, pic_stats_t* out);
 pic_status pic_batch_set_timing(pic_batch* batch, int on);
 const char* pic_batch_last_error(const pic_batch* batch);
@@ -260,7 +305,8 @@ pic_status pic_batch_destroy(pic_batch* batch);
 
 /* ---- Serving: a request loop over a batch --------------------------------
  * A server owns one batch and one worker thread.  Run requests are queued
- * when submitted and admitted in arrival order while a batch slot is free and
+ * when submitted and admitted (in arrival order by default, see
+ * pic_server_set_policy) while a batch slot is free and
  * the run's footprint (pic_batch_run_footprint) fits the device-memory
  * budget (hbm_budget_bytes of the pic_config; 0: no budget).  Admitted runs
  * join the running batch between step chunks (continuous batching: a request
@@ -301,11 +347,48 @@ pic_status pic_server_submit(pic_server* srv, const pic_run_desc* desc, int nbin
  * returns its error (and is forgotten).  PIC_ERR_INVALID_ARG: unknown ticket. */
 pic_status pic_server_result(pic_server* srv, int64_t ticket, double wait_s, double* ion_counts, double* el_counts,
                              double* energy, double* latency_s);
+/* Admission policy: PIC_SERVE_FIFO (arrival order, the default) or
+ * PIC_SERVE_SHORTEST_FIRST (least particles x steps first, ties in arrival
+ * order); max_resident_particles (0: no cap) bounds the particles stepping
+ * at once, so that admitted runs are not slowed by an ever larger batch
+ * (a request is always admitted when nothing is running). */
+enum { PIC_SERVE_FIFO = 0, PIC_SERVE_SHORTEST_FIRST = 1 };
+pic_status pic_server_set_policy(pic_server* srv, int policy, int64_t max_resident_particles);
 pic_status pic_server_stats(pic_server* srv, pic_server_stats_t* out);
 /* Message of the last failed server call of the calling thread. */
 const char* pic_server_last_error(const pic_server* srv);
 /* Stop the worker (unfinished requests are dropped) and free everything. */
 pic_status pic_server_destroy(pic_server* srv);
+
+/* ---- Single electrons in analytic plane waves (the paper's validation path) --
+ * Integrates many independent electrons (charge -1) at once, one GPU thread
+ * each, in double precision: a reference integrator for scans over
+ * amplitude and initial momentum, as in Sec. 3 (the paper's single-particle
+ * test against the lab-frame LL equation), not the PIC step.
+ * Plane waves travel along +x with phase phi = t - x and B = x_hat x E:
+ *   wave 0: LP, Ey = a0 cos(phi);
+ *   wave 1: CP, (Ey, Ez) = (a0/sqrt2) (cos(phi), sin(phi));
+ *   wave 2: LP pulse, Ey = a0 sin^2(pi phi/tau) cos(phi) for 0 <= phi <= tau, else 0.
+ * Integrators: PIC_INTEGRATOR_LEAPFROG, the pusher of Sec. 3 (Boris + the RR
+ * kick of Eqs. f_r, pertfull, estim1, estimgamma; initial data x(0) = x0 and
+ * p^{-1/2} = p0; rows hold t_{n+1}, x^{n+1}, p^{n+1/2}); PIC_INTEGRATOR_RK4,
+ * classical RK4 on Eq. (3dLL) (x(0) = x0, p(0) = p0; rows hold t, x, p at the
+ * same time).  flags: PIC_ELECTRON_RR adds radiation reaction (eps from
+ * lambda_um); PIC_ELECTRON_DERIV keeps the field-derivative term of
+ * Eq. (3dLL) (RK4 only).  out: caller-owned host array [n][nsamples][5], row k
+ * of case c taken after (k+1)*every steps (nsamples <= nsteps/every).
+ * Synchronous. */
+typedef struct {
+    int wave;        /* 0, 1 or 2 as above */
+    double a0, tau;  /* amplitude; pulse length in 1/omega (wave 2) */
+    double x0;       /* initial position, c/omega */
+    double p0[3];    /* initial momentum, m c */
+} pic_electron_case;
+enum { PIC_INTEGRATOR_LEAPFROG = 0, PIC_INTEGRATOR_RK4 = 1 };
+enum { PIC_ELECTRON_RR = 1, PIC_ELECTRON_DERIV = 2 };
+pic_status pic_electron_scan(const pic_electron_case* cases, int64_t n, int integrator, int flags, double dt,
+                             int64_t nsteps, int every, double lambda_um, int device, double* out,
+                             int64_t nsamples);
 
 /* ---- Spectrum without device allocation -----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of

@@ -28,6 +28,11 @@ ELECTRON, ION = 0, 1
 EX, EY, EZ, BY, BZ, JX, JY, JZ = range(8)
 
 
+def ecr(lambda_um):
+    """E_cr = m c^2/(hbar omega) in the field unit m omega c/|e|."""
+    return lib().or_ecr(lambda_um)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (ISO C11, -O2, no FP contraction)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
@@ -93,6 +98,10 @@ def lib():
         L.or_read_particles.restype = C.c_int64
         L.or_read_particles.argtypes = [C.c_void_p, C.c_int, C.c_int64, dp, dp, dp, dp,
                                         C.POINTER(C.c_int32)]
+        L.or_snapshot.restype = C.c_int64
+        L.or_snapshot.argtypes = [C.c_void_p, C.c_int, C.c_int64, dp, dp]
+        L.or_ecr.restype = C.c_double
+        L.or_ecr.argtypes = [C.c_double]
         L.or_read_fields.restype = C.c_int64
         L.or_read_fields.argtypes = [C.c_void_p, C.c_int, C.c_int64, dp]
         _lib = L
@@ -209,6 +218,13 @@ class OracleSim:
         self._check(self._L.or_spectra(self._h, species, nbins, e_min, e_max, _dp(counts),
                                        _dp(uo)), "spectra")
         return counts, uo
+
+    def snapshot(self, species):
+        """Friction coefficient d (Eq. damping) and quantum parameter chi per particle."""
+        n = self._L.or_snapshot(self._h, species, 0, None, None)
+        d, chi = np.zeros(n), np.zeros(n)
+        self._L.or_snapshot(self._h, species, n, _dp(d), _dp(chi))
+        return dict(d=d, chi=chi)
 
     def particles(self, species):
         n = self._L.or_read_particles(self._h, species, 0, None, None, None, None, None)

@@ -130,6 +130,21 @@ int or_spectra(const or_sim* s, int species, int nbins, double e_min, double e_m
 int64_t or_read_particles(const or_sim* s, int species, int64_t cap, double* x,
                           double* px, double* py, double* pz, int32_t* flag);
 
+/* Skin-layer observables of Sec. 4 (Figs. 2 and 4) per particle, in load
+ * order, at the current step: the friction coefficient
+ *   d = eps gamma^2 [E^2 - (v.E)^2 + v^2 B^2 - (v.B)^2 - 2 v.(E x B)]
+ * of Eq. (damping), and the quantum parameter
+ *   chi = gamma sqrt(E^2 - (v.E)^2 + v^2 B^2 - (v.B)^2 - 2 v.(E x B)) / E_cr,
+ * E_cr = m c^2 / (hbar omega) in field units, whose plane-wave value for a
+ * particle crossing the wave is the gamma sqrt(I/I_cr) of the classical
+ * validity condition (Sec. 2).  Fields E^n, B^n gathered at x^n as the push
+ * gathers them; v from the stored momentum p^{n-1/2}.  Frozen particles get
+ * 0.  d, chi nullable.  Returns the count, or -1. */
+int64_t or_snapshot(const or_sim* s, int species, int64_t cap, double* d, double* chi);
+
+/* E_cr in field units m_e omega c/|e| for wavelength lambda_um. */
+double or_ecr(double lambda_um);
+
 /* comp: 0 Ex, 1 Ey, 2 Ez, 3 By, 4 Bz, 5 Jx, 6 Jy, 7 Jz (J of the last step).
  * Returns the number of values written, or -1. */
 int64_t or_read_fields(const or_sim* s, int comp, int64_t cap, double* out);

@@ -26,7 +26,15 @@
 #define OR_MP_ME 1836.15267343
 #define OR_MU_ME 1822.888486209
 
+/* Reduced Compton wavelength hbar/(m_e c) in micrometres (CODATA 2018:
+ * 3.8615926796e-13 m); the paper quotes 3.9e-7 um in Sec. 2. */
+#define OR_LAMBDAC_UM 3.8615926796e-7
+
 double or_eps_rr(double lambda_um) { return (4.0 / 3.0) * OR_PI * OR_RE_UM / lambda_um; }
+
+/* E_cr = m^2 c^3/(hbar |e|) over the field unit m omega c/|e| is
+ * m c^2/(hbar omega) = lambda / (2 pi hbar/(m c)). */
+double or_ecr(double lambda_um) { return lambda_um / (2.0 * OR_PI * OR_LAMBDAC_UM); }
 
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
@@ -216,7 +224,7 @@ typedef struct {
 
 struct or_sim {
     int Nx, is;
-    double dx, dt, cfl, eps;
+    double dx, dt, cfl, eps, lambda_um;
     int rr_on;
     double *mem, *Ex, *Ey, *Ez, *By, *Bz, *Jx, *Jy, *Jz;
     or_species sp[2];
@@ -244,6 +252,7 @@ or_sim* or_create(const or_config* cfg) {
     s->cfl = cfg->cfl;
     s->dt = cfg->cfl * s->dx;
     s->eps = or_eps_rr(cfg->lambda_um);
+    s->lambda_um = cfg->lambda_um;
     s->rr_on = cfg->rr_on ? 1 : 0;
     size_t len = (size_t)s->Nx + 1 + 2 * OR_PAD;
     s->mem = (double*)calloc(8 * len, sizeof(double));
@@ -624,6 +633,33 @@ int64_t or_read_particles(const or_sim* s, int species, int64_t cap, double* x, 
         if (py) py[i] = sp->py[i];
         if (pz) pz[i] = sp->pz[i];
         if (flag) flag[i] = sp->flag[i];
+    }
+    return sp->n;
+}
+
+int64_t or_snapshot(const or_sim* s, int species, int64_t cap, double* d, double* chi) {
+    if (!s || species < 0 || species > 1) return -1;
+    const or_species* sp = &s->sp[species];
+    const double ecr = or_ecr(s->lambda_um);
+    int64_t n = sp->n < cap ? sp->n : cap;
+    for (int64_t i = 0; i < n; i++) {
+        double dv = 0.0, cv = 0.0;
+        if (!sp->flag[i]) {
+            double E[3], B[3], p[3] = {sp->px[i], sp->py[i], sp->pz[i]};
+            gather(s, sp->xi[i], E, B);
+            double g = sqrt(1.0 + dot3(p, p));
+            double v[3] = {p[0] / g, p[1] / g, p[2] / g};
+            double ExB[3];
+            cross3(E, B, ExB);
+            double vE = dot3(v, E), vB = dot3(v, B);
+            /* the bracket of Eq. (damping), first form */
+            double br = dot3(E, E) - vE * vE + dot3(v, v) * dot3(B, B) - vB * vB - 2.0 * dot3(v, ExB);
+            if (br < 0.0) br = 0.0; /* >= 0 exactly; rounding only */
+            dv = s->eps * g * g * br;
+            cv = g * sqrt(br) / ecr;
+        }
+        if (d) d[i] = dv;
+        if (chi) chi[i] = cv;
     }
     return sp->n;
 }

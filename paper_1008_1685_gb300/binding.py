@@ -15,6 +15,7 @@ _LIB_PATH = os.path.join(_HERE, "libpicrr.so")
 
 LP, CP = 0, 1
 ENV_SIN2, ENV_TRAPEZOID = 0, 1
+SERVE_FIFO, SERVE_SHORTEST_FIRST = 0, 1
 ELECTRON, ION = 0, 1
 EX, EY, EZ, BY, BZ, JX, JY, JZ = range(8)
 
@@ -31,7 +32,10 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_batch_read_particles", "pic_batch_read_fields", "pic_batch_release_run", "pic_batch_stats",
            "pic_batch_set_timing", "pic_batch_last_error", "pic_batch_destroy", "pic_batch_run_footprint",
            "pic_server_create", "pic_server_submit", "pic_server_result", "pic_server_stats",
-           "pic_server_last_error", "pic_server_destroy")
+           "pic_server_last_error", "pic_server_destroy", "pic_tune_shapes",
+           "pic_batch_tune_shapes", "pic_set_shapes", "pic_batch_set_shapes", "pic_server_set_policy",
+           "pic_snapshot", "pic_batch_snapshot",
+           "pic_electron_scan")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -54,6 +58,15 @@ class Config(C.Structure):
         ("source_node", C.c_int),
         ("hbm_budget_bytes", C.c_size_t),
     ]
+
+
+class ElectronCase(C.Structure):
+    _fields_ = [("wave", C.c_int), ("a0", C.c_double), ("tau", C.c_double), ("x0", C.c_double),
+                ("p0", C.c_double * 3)]
+
+
+INTEGRATOR_LEAPFROG, INTEGRATOR_RK4 = 0, 1
+ELECTRON_RR, ELECTRON_DERIV = 1, 2
 
 
 class RunDesc(C.Structure):
@@ -170,11 +183,45 @@ def library():
         L.pic_server_last_error.argtypes = [vp]
         L.pic_server_last_error.restype = C.c_char_p
         L.pic_server_destroy.argtypes = [vp]
+        L.pic_tune_shapes.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.pic_batch_tune_shapes.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.pic_set_shapes.argtypes = [vp, C.c_int, C.c_int]
+        L.pic_batch_set_shapes.argtypes = [vp, C.c_int, C.c_int]
+        L.pic_server_set_policy.argtypes = [vp, C.c_int, i64]
+        L.pic_electron_scan.argtypes = [C.POINTER(ElectronCase), i64, C.c_int, C.c_int, C.c_double, i64, C.c_int,
+                                        C.c_double, C.c_int, dp, i64]
+        L.pic_snapshot.argtypes = [vp, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp, C.POINTER(i64)]
+        L.pic_batch_snapshot.argtypes = [vp, C.c_int, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp,
+                                         C.POINTER(i64)]
         for name in SYMBOLS:
             if name not in ("pic_last_error", "pic_batch_last_error", "pic_server_last_error"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
+
+
+def electron_scan(cases, integrator=INTEGRATOR_RK4, rr=True, deriv=False, dt=0.01, nsteps=1000, every=1,
+                  lambda_um=0.8, device=0):
+    """Single electrons in analytic plane waves on the GPU (pic_electron_scan).
+    cases: iterable of dicts with wave, a0, x0, p0 (3) and tau (wave 2).
+    Returns an array [n][nsteps // every][5] of rows (t, x, px, py, pz)."""
+    cases = list(cases)
+    arr = (ElectronCase * max(1, len(cases)))()
+    for k, c in enumerate(cases):
+        arr[k].wave = int(c["wave"])
+        arr[k].a0 = float(c["a0"])
+        arr[k].tau = float(c.get("tau", 0.0))
+        arr[k].x0 = float(c.get("x0", 0.0))
+        for j in range(3):
+            arr[k].p0[j] = float(c["p0"][j])
+    ns = nsteps // every
+    out = np.zeros((len(cases), ns, 5))
+    flags = (ELECTRON_RR if rr else 0) | (ELECTRON_DERIV if deriv else 0)
+    rc = library().pic_electron_scan(arr, len(cases), integrator, flags, dt, nsteps, every, lambda_um, device,
+                                     _dp(out), ns)
+    if rc != 0:
+        raise PicError(rc, library().pic_last_error(None).decode())
+    return out
 
 
 def spectrum_noalloc(px_ptr, py_ptr, pz_ptr, n, mass_me, weight_dx, nbins, e_min, e_max, counts_ptr,
@@ -193,6 +240,19 @@ def _dp(a):
 
 def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _snapshot(call, check, per_particle):
+    n = C.c_int64(0)
+    summ = np.zeros(3)
+    check(call(0, None, None, None, None, None, _dp(summ), C.byref(n)))
+    out = dict(d_max=summ[0], chi_max=summ[1], n_flagged=int(summ[2]), n=n.value)
+    if per_particle and n.value:
+        arr = {k: np.zeros(n.value) for k in ("x", "px", "pperp", "d", "chi")}
+        check(call(n.value, _dp(arr["x"]), _dp(arr["px"]), _dp(arr["pperp"]), _dp(arr["d"]), _dp(arr["chi"]), None,
+                   None))
+        out.update(arr)
+    return out
 
 
 class Sim:
@@ -294,6 +354,11 @@ class Sim:
                                                flag.ctypes.data_as(C.POINTER(C.c_int32)), None))
         return dict(x=x, px=px, py=py, pz=pz, flag=flag)
 
+    def snapshot(self, species, chi_flag=0.1, per_particle=True):
+        """d (Eq. damping) and chi per particle (load order) with x, p_x, p_perp,
+        and the summary (max d, max chi, particles with chi >= chi_flag)."""
+        return _snapshot(lambda *a: self._L.pic_snapshot(self._h, species, chi_flag, *a), self._check, per_particle)
+
     def field(self, comp):
         out = np.zeros(self.nx + 1)
         n = C.c_int64(0)
@@ -304,6 +369,17 @@ class Sim:
         st = Stats()
         self._check(self._L.pic_stats(self._h, C.byref(st)))
         return st.as_dict()
+
+    def tune_shapes(self, steps_per_candidate=64):
+        """Pick the fastest work-unit size and sort interval by timing real steps.
+        Returns (unit_particles, sort_interval, ms_per_step[8])."""
+        u, c = C.c_int(0), C.c_int(0)
+        ms = np.full(8, -1.0)
+        self._check(self._L.pic_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), _dp(ms)))
+        return u.value, c.value, ms
+
+    def set_shapes(self, unit_particles, sort_interval):
+        self._check(self._L.pic_set_shapes(self._h, unit_particles, sort_interval))
 
     def set_timing(self, on=True):
         self._check(self._L.pic_set_timing(self._h, int(on)))
@@ -392,6 +468,10 @@ class Batch:
                                                      flag.ctypes.data_as(C.POINTER(C.c_int32)), None))
         return dict(x=x, px=px, py=py, pz=pz, flag=flag)
 
+    def snapshot(self, run, species, chi_flag=0.1, per_particle=True):
+        return _snapshot(lambda *a: self._L.pic_batch_snapshot(self._h, run, species, chi_flag, *a), self._check,
+                         per_particle)
+
     def nx(self, run):
         return self._nx[run]
 
@@ -416,6 +496,15 @@ class Batch:
         st = Stats()
         self._check(self._L.pic_batch_stats(self._h, C.byref(st)))
         return st.as_dict()
+
+    def tune_shapes(self, steps_per_candidate=64):
+        u, c = C.c_int(0), C.c_int(0)
+        ms = np.full(8, -1.0)
+        self._check(self._L.pic_batch_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), _dp(ms)))
+        return u.value, c.value, ms
+
+    def set_shapes(self, unit_particles, sort_interval):
+        self._check(self._L.pic_batch_set_shapes(self._h, unit_particles, sort_interval))
 
     def set_timing(self, on=True):
         self._check(self._L.pic_batch_set_timing(self._h, int(on)))
@@ -471,6 +560,11 @@ class Server:
         if rc != 0:
             raise self._err(rc)
         return dict(ion=ion, el=el, energy=en, latency_s=lat.value)
+
+    def set_policy(self, policy=SERVE_FIFO, max_resident_particles=0):
+        rc = self._L.pic_server_set_policy(self._h, policy, max_resident_particles)
+        if rc != 0:
+            raise self._err(rc)
 
     def stats(self):
         st = ServerStats()

@@ -1,6 +1,8 @@
 // Diagnostics: field and kinetic energy (FP64 accumulation, fixed-order
-// reductions so repeated calls give identical bits) and the kinetic-energy
-// spectrum (integer bin counts).
+// reductions so repeated calls give identical bits), the kinetic-energy
+// spectrum (integer bin counts), and the skin-layer snapshot of Sec. 4: the
+// friction coefficient d of Eq. (damping) and the quantum parameter chi of
+// the classical validity condition (Sec. 2) for every particle.
 #include "picrr_internal.cuh"
 
 namespace picrr {
@@ -108,7 +110,58 @@ __global__ void __launch_bounds__(DIAG_T) k_spectrum(DevSpecies sp, int64_t n, d
             if (sh[i]) atomicAdd(&bins[i], static_cast<unsigned long long>(sh[i]));
 }
 
+// One thread per particle.  Linear gather as in the push (nodes for Ey, Ez;
+// half nodes for Ex, By, Bz; zero guard elements beyond the grid), then
+// gamma^2 [f_L^2 - (v.f_L)^2] as the sum of squares f_L^2 + |p x f_L|^2
+// (Lagrange identity with p = gamma v).
+__global__ void __launch_bounds__(DIAG_T) k_snapshot(DevSpecies sp, int64_t n, const SnapParams S, float* d_out,
+                                                     float* chi_out, unsigned long long* out) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * DIAG_T + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * DIAG_T) {
+        const int c = sp.cell[i];
+        float d = 0.f, chi = 0.f;
+        if (c >= 0) {  // frozen particles (c < 0) feel no field
+            const float f = sp.off[i];
+            const int q = c + PADF;
+            const float e_y = (1.f - f) * S.F[1][q] + f * S.F[1][q + 1];
+            const float e_z = (1.f - f) * S.F[2][q] + f * S.F[2][q + 1];
+            const float h = f - 0.5f;
+            const int jb = h < 0.f ? q - 1 : q;
+            const float g = h < 0.f ? h + 1.f : h;
+            const float e_x = (1.f - g) * S.F[0][jb] + g * S.F[0][jb + 1];
+            const float b_y = (1.f - g) * S.F[3][jb] + g * S.F[3][jb + 1];
+            const float b_z = (1.f - g) * S.F[4][jb] + g * S.F[4][jb + 1];
+            const float px = sp.px[i], py = sp.py[i], pz = sp.pz[i];
+            const float ig = rsqrtf(1.f + px * px + py * py + pz * pz);
+            const float vx = px * ig, vy = py * ig, vz = pz * ig;
+            const float fx = -(e_x + vy * b_z - vz * b_y);
+            const float fy = -(e_y - vx * b_z);
+            const float fz = -(e_z + vx * b_y);
+            const float cx = py * fz - pz * fy, cy = pz * fx - px * fz, cz = px * fy - py * fx;
+            const float br = fx * fx + fy * fy + fz * fz + cx * cx + cy * cy + cz * cz;
+            d = S.eps * br;
+            chi = sqrtf(br) * S.ecr_inv;
+        }
+        if (d_out) d_out[i] = d;
+        if (chi_out) chi_out[i] = chi;
+        // maxima of non-negative floats through their bit patterns; integer count
+        atomicMax(reinterpret_cast<unsigned int*>(&out[0]), __float_as_uint(d));
+        atomicMax(reinterpret_cast<unsigned int*>(&out[1]), __float_as_uint(chi));
+        const unsigned flagged = __ballot_sync(__activemask(), chi >= S.chi_flag);
+        if (flagged && (threadIdx.x & 31) == __ffs(__activemask()) - 1)
+            atomicAdd(&out[2], static_cast<unsigned long long>(__popc(flagged)));
+    }
+}
+
 }  // namespace
+
+void launch_snapshot(DevSpecies sp, int64_t n, const SnapParams& S, float* d_out, float* chi_out,
+                     unsigned long long* out, cudaStream_t st) {
+    int64_t g = (n + DIAG_T - 1) / DIAG_T;
+    if (g > 4864) g = 4864;
+    if (g < 1) g = 1;
+    k_snapshot<<<static_cast<int>(g), DIAG_T, 0, st>>>(sp, n, S, d_out, chi_out, out);
+}
 
 int launch_field_energy(const DiagParams& D, double* partials, int max_blocks, cudaStream_t st) {
     int g = (D.Nx + 1 + DIAG_T - 1) / DIAG_T;

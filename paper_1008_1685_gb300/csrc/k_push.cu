@@ -1,8 +1,9 @@
 // Fused field gather + Boris push + Landau-Lifshitz radiation-reaction kick
 // + move + charge-conserving deposit (the particle part of one PIC step).
 //
-// One CTA per work unit (<= UNIT_P consecutive particles of one species
-// whose cells at the last sort lie in one tile).  Because cfl < 1 a particle
+// One CTA per work unit (at most unit_p consecutive particles of one species
+// whose cells at the last sort lie in one tile, or in one group of sparse
+// tiles holding at most unit_p particles; unit_p is a shape of the batch).  Because cfl < 1 a particle
 // moves less than one cell per step, so k steps after the sort every
 // particle of the unit lies in [lo - k, hi + k]; the CTA stages the fields of
 // the window [lo - k - 1, hi + k + 2] into shared memory with one bulk TMA
@@ -213,18 +214,11 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
                 const float ign = rsqrtf(1.f + px * px + py * py + pz * pz);
                 const float vxn = px * ign, vyn = py * ign, vzn = pz * ign;
                 float fn = f + cfl * vxn;
-                int d = 0;
-                if (fn >= 1.f) {
-                    fn -= 1.f;
-                    d = 1;
-                } else if (fn < 0.f) {
-                    fn += 1.f;
-                    d = -1;
-                    if (fn >= 1.f) {  // rounded up to the boundary: same point as (c, 0)
-                        fn = 0.f;
-                        d = 0;
-                    }
-                }
+                int d = fn >= 1.f ? 1 : (fn < 0.f ? -1 : 0);
+                fn -= static_cast<float>(d);
+                const bool edge = fn >= 1.f;  // rounded up to the boundary: same point as (c, 0)
+                d = edge ? 0 : d;
+                fn = edge ? 0.f : fn;
                 int cnew = c + d, store_c = cnew;
                 if (cnew < 0) {  // frozen at x = 0 (sorts under cell 0)
                     cnew = 0;
@@ -239,24 +233,21 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
                 // --- deposit records (old bin lb, new bin lb + d)
                 const float ay = 0.5f * qw * vyn, az = 0.5f * qw * vzn;
                 ko = lb;
-                if (d == 0) {
-                    vo0 = ay * ((1.f - f) + (1.f - fn));
-                    vo1 = ay * (f + fn);
-                    vo2 = az * ((1.f - f) + (1.f - fn));
-                    vo3 = az * (f + fn);
-                    vo4 = jxf * (fn - f);
-                } else {
-                    kn = lb + d;
-                    vo0 = ay * (1.f - f);
-                    vo1 = ay * f;
-                    vo2 = az * (1.f - f);
-                    vo3 = az * f;
-                    vo4 = d > 0 ? jxf * (1.f - f) : -jxf * f;
-                    vn0 = ay * (1.f - fn);
+                {
+                    const bool cross = d != 0;
+                    const float g0 = 1.f - f, g1 = 1.f - fn;
+                    const float wlo = cross ? g0 : g0 + g1, whi = cross ? f : f + fn;
+                    vo0 = ay * wlo;
+                    vo1 = ay * whi;
+                    vo2 = az * wlo;
+                    vo3 = az * whi;
+                    vo4 = cross ? (d > 0 ? jxf * g0 : -jxf * f) : jxf * (fn - f);
+                    kn = cross ? lb + d : -1;
+                    vn0 = ay * g1;
                     vn1 = ay * fn;
-                    vn2 = az * (1.f - fn);
+                    vn2 = az * g1;
                     vn3 = az * fn;
-                    vn4 = d > 0 ? jxf * fn : -jxf * (1.f - fn);
+                    vn4 = d > 0 ? jxf * fn : -jxf * g1;
                 }
                 c = store_c;
                 f = fn;

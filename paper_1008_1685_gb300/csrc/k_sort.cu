@@ -17,7 +17,9 @@
 //      per-warp counts combined in warp order), so the result does not depend
 //      on scheduling;
 //   4. the unit table is rebuilt from the sorted cells: tiles of TILE cells,
-//      split into chunks of at most UNIT_P particles.
+//      split into chunks of at most unit_p particles, except that GROUP
+//      consecutive tiles holding at most unit_p particles together form one
+//      unit (sparse regions would otherwise give many nearly empty units).
 // Every particle is read once and written once; the cell array is read once
 // more for the counts.
 #include <algorithm>
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(SORT_T) k_sort_count(const SortParams S) {
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SSTR; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = cnt[i];
+    for (int i = threadIdx.x; i < L; i += SORT_T) S.cnt[static_cast<size_t>(u) * SSTR + i] = cnt[i];
 }
 
 // Units of run `run`, species s whose window covers cell `key`: [u0, u1].
@@ -276,8 +278,9 @@ __global__ void __launch_bounds__(SORT_T) k_sort_scatter(const SortParams S) {
         }
     }
     __syncthreads();
-    // per cell: destination start of each warp's particles, in warp order
-    for (int l = tid; l < SSTR; l += SORT_T) {
+    // per cell of the window: destination start of each warp's particles, in warp order
+    const int L = S.units.hi[u] + S.k + 1 - wb;
+    for (int l = tid; l < L && l < SSTR; l += SORT_T) {
         int run = S.offs[static_cast<size_t>(u) * SSTR + l];
 #pragma unroll
         for (int w = 0; w < SC_W; ++w) {
@@ -342,8 +345,18 @@ __global__ void __launch_bounds__(SCAN_T) k_tile_units(const SortParams S) {
     const int ntiles = (R.Nx + TILE - 1) / TILE;
     const int32_t* ks = R.keystart[s];
     for (int t = threadIdx.x; t < ntiles; t += SCAN_T) {
-        const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
-        R.tile_n[s][t] = (te - ts + UNIT_P - 1) / UNIT_P;
+        // a group of GROUP tiles holding at most unit_p particles is one unit,
+        // counted on its first tile; otherwise each tile is split on its own
+        const int g0 = (t / GROUP) * SPAN;
+        const int gn = ks[min(g0 + SPAN, R.Nx)] - ks[g0];
+        int n;
+        if (gn <= S.unit_p) {
+            n = (t % GROUP == 0 && gn > 0) ? 1 : 0;
+        } else {
+            const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
+            n = (te - ts + S.unit_p - 1) / S.unit_p;
+        }
+        R.tile_n[s][t] = n;
     }
     __syncthreads();
     const int nu = block_scan_ranges(R.tile_n[s], R.tile_first[s], ntiles, sh);
@@ -385,9 +398,17 @@ __global__ void k_fill_units(const SortParams S, int ubuf) {
     }
     const int t = a0;
     const int32_t* ks = R.keystart[s];
-    const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
-    const int a = ts + (v - tf[t]) * UNIT_P;
-    const int b = min(a + UNIT_P, te);
+    const int g0 = (t / GROUP) * SPAN;
+    const int gs = ks[g0], ge = ks[min(g0 + SPAN, R.Nx)];
+    int a, b;
+    if (ge - gs <= S.unit_p) {  // the whole group (t is its first tile)
+        a = gs;
+        b = ge;
+    } else {
+        const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
+        a = ts + (v - tf[t]) * S.unit_p;
+        b = min(a + S.unit_p, te);
+    }
     const int32_t* cell = R.sp[s][ubuf].cell;
     S.units.run[u] = run;
     S.units.species[u] = s;

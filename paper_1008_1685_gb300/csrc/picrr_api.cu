@@ -9,6 +9,7 @@
 // step loop (push kernel, Yee kernel, periodic sort), read-backs and
 // counters.  See include/picrr.h for the contract of every entry point.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,7 @@ constexpr double kReUm = 2.8179403262e-9;   // classical electron radius, um (CO
 constexpr double kMec2MeV = 0.51099895000;  // electron rest energy, MeV
 constexpr double kMpMe = 1836.15267343;     // proton mass / electron mass
 constexpr double kMuMe = 1822.888486209;    // atomic mass unit / electron mass
+constexpr double kLambdaCUm = 3.8615926796e-7;  // reduced Compton wavelength hbar/(m_e c), um (CODATA 2018)
 constexpr int kMaxDiagBlocks = 1024;
 constexpr int kIncRing = 16;                // slots of the laser-source upload ring (one chunk of steps each)
 
@@ -114,6 +116,7 @@ struct RunHost {
 struct Batch {
     pic_config cfg{};
     int device = 0, sort_interval = 8, max_runs = 1;
+    int unit_p = UNIT_P;  // particles per work unit at most (a run-time shape)
     double dx = 0, dt = 0, cfl = 0, eps = 0;
     cudaStream_t stream = nullptr, own_stream = nullptr;
     size_t bytes = 0, budget = 0;
@@ -125,8 +128,8 @@ struct Batch {
     int32_t* d_blk_run = nullptr;
     int32_t* d_blk_i0 = nullptr;
     int nblk = 0, blk_cap = 0;
-    float* d_inc = nullptr;  // [sort_interval][max_runs * 6]
-    float* h_inc = nullptr;  // pinned ring [kIncRing][sort_interval][max_runs * 6]
+    float* d_inc = nullptr;  // [KMAX][max_runs * 6]
+    float* h_inc = nullptr;  // pinned ring [kIncRing][KMAX][max_runs * 6]
     cudaEvent_t inc_ev[kIncRing] = {};
     int inc_slot = 0;
 
@@ -148,6 +151,7 @@ struct Batch {
     int* d_status = nullptr;
     double* diag_partials = nullptr;
     double* diag_out = nullptr;
+    unsigned long long* snap_out = nullptr;  // [4]: max d bits, max chi bits, flagged count
     unsigned long long* bins = nullptr;
     int bins_cap = 0;
 
@@ -317,8 +321,7 @@ pic_status batch_create(const pic_config* cfg, int max_runs, Batch** out) {
     *out = nullptr;
     pic_status st = validate_common(cfg);
     if (st != PIC_OK) return st;
-    if (max_runs < 1 || max_runs > (1 << 16))
-        return fail(nullptr, PIC_ERR_INVALID_ARG, "max_runs must be in [1, 65536]");
+    if (max_runs < 1 || max_runs > 8192) return fail(nullptr, PIC_ERR_INVALID_ARG, "max_runs must be in [1, 8192]");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -344,17 +347,18 @@ pic_status batch_create(const pic_config* cfg, int max_runs, Batch** out) {
     }
     b->stream = b->own_stream;
     if ((st = dalloc_t(b, b->mem, &b->d_runs, static_cast<size_t>(max_runs))) != PIC_OK ||
-        (st = dalloc_t(b, b->mem, &b->d_inc, static_cast<size_t>(max_runs) * 6 * b->sort_interval)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->d_inc, static_cast<size_t>(max_runs) * 6 * KMAX)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->d_status, 4)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->diag_partials, kMaxDiagBlocks)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->diag_out, 8)) != PIC_OK ||
+        (st = dalloc_t(b, b->mem, &b->snap_out, 4)) != PIC_OK ||
         (st = dalloc_t(b, b->mem, &b->rs_units, static_cast<size_t>(4) * max_runs)) != PIC_OK) {
         g_null_error = b->err;
         batch_destroy(b);
         return st;
     }
     if (cudaMallocHost(&b->h_runs, sizeof(RunDev) * max_runs) != cudaSuccess ||
-        cudaMallocHost(&b->h_inc, sizeof(float) * 6 * max_runs * b->sort_interval * kIncRing) != cudaSuccess) {
+        cudaMallocHost(&b->h_inc, sizeof(float) * 6 * max_runs * KMAX * kIncRing) != cudaSuccess) {
         cudaGetLastError();
         batch_destroy(b);
         return fail(nullptr, PIC_ERR_OOM, "pinned host allocation failed");
@@ -470,7 +474,7 @@ size_t run_footprint(const Batch* b, double length_lambda, int64_t n) {
     const size_t cap = static_cast<size_t>((n + 3) / 4 * 4 + 8);
     t += 2 * 2 * 6 * rounded(cap * 4);
     const int64_t ntiles = (Nx + TILE - 1) / TILE;
-    const size_t units = static_cast<size_t>(2 * ((n + UNIT_P - 1) / UNIT_P + ntiles + 1));
+    const size_t units = static_cast<size_t>(2 * ((n + UNIT_P_MIN - 1) / UNIT_P_MIN + ntiles + 1));
     t += units * (6 * 4 + 8 + 2 * SSTR * 4) * 3 / 2;
     t += static_cast<size_t>(Nx / FIELD_T + 1) * 8 * 3 / 2;
     return t;
@@ -701,10 +705,10 @@ void finalize_run_params(Batch* b, RunHost& r) {
     r.fp_bits = std::max(8, std::min(52, fp));
     d.fp_inv = std::ldexp(1.0f, -r.fp_bits);
     for (int s = 0; s < 2; ++s) {
-        // a warp record sums at most 16 particles of one lane (a thread holds at most
-        // UNIT_P / PUSH_T + 4 particles of a unit) over 32 lanes, each value bounded by
-        // |q w| max(1, 1/cfl): keep every lane below 2^26
-        static_assert(UNIT_P / PUSH_T + 4 <= 16, "running record bound");
+        // a lane's running record merges at most the 4 particles of one 16-byte slot
+        // (records are flushed at the end of every round); with a margin of 4 the
+        // bound below takes 16 particles of one lane over 32 lanes, each value
+        // bounded by |q w| max(1, 1/cfl), and keeps every lane below 2^26
         const double vmax = r.sp[s].loaded ? std::fabs(r.sp[s].q * r.sp[s].w) * std::max(1.0, 1.0 / b->cfl) : 0.0;
         int ls = 40;
         if (vmax > 0.0) ls = static_cast<int>(std::floor(26.0 - std::log2(16.0 * vmax)));
@@ -773,6 +777,7 @@ SortParams sort_params(Batch* b) {
     for (auto& r : b->runs)
         if (r.used) mx = std::max(mx, r.Nx);
     S.kb_max = (mx + KEY_T - 1) / KEY_T;
+    S.unit_p = b->unit_p;
     return S;
 }
 
@@ -883,7 +888,7 @@ pic_status activate_pending(Batch* b) {
         if (!r.started) joining.push_back(i);
         const int ntiles = (r.Nx + TILE - 1) / TILE;
         for (int s = 0; s < 2; ++s)
-            if (r.sp[s].loaded) need += (r.sp[s].n + UNIT_P - 1) / UNIT_P + ntiles + 1;
+            if (r.sp[s].loaded) need += (r.sp[s].n + b->unit_p - 1) / b->unit_p + ntiles + 1;
     }
     if (need > (1 << 30)) return fail(b, PIC_ERR_INVALID_ARG, "too many work units");
     st = ensure_units(b, static_cast<int>(need));
@@ -923,7 +928,7 @@ void deactivate(Batch* b, int id) {
 // uploaded through a pinned ring: step j of the chunk reads d_inc + j * 6 * max_runs.
 pic_status upload_incident(Batch* b, int steps) {
     const size_t per_step = static_cast<size_t>(6) * b->max_runs;
-    float* h = b->h_inc + static_cast<size_t>(b->inc_slot) * per_step * b->sort_interval;
+    float* h = b->h_inc + static_cast<size_t>(b->inc_slot) * per_step * KMAX;
     PIC_CK(b, cudaEventSynchronize(b->inc_ev[b->inc_slot]));
     for (int j = 0; j < steps; ++j) {
         float* hj = h + j * per_step;
@@ -1105,6 +1110,110 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
     return PIC_OK;
 }
 
+// Units a batch can need with unit size unit_p (each tile adds at most one
+// partial unit; merged groups only lower the count).
+int64_t units_needed(const Batch* b, int unit_p) {
+    int64_t need = 1;
+    for (const auto& r : b->runs) {
+        if (!r.used || !r.active) continue;
+        const int ntiles = (r.Nx + TILE - 1) / TILE;
+        for (int s = 0; s < 2; ++s)
+            if (r.sp[s].loaded) need += (r.sp[s].n + unit_p - 1) / unit_p + ntiles + 1;
+    }
+    return need;
+}
+
+// Set the launch shapes: work-unit size (takes effect through a sort now, which
+// rebuilds the unit table) and sort interval.
+pic_status set_shapes(Batch* b, int unit_p, int interval) {
+    if (unit_p < UNIT_P_MIN || unit_p > UNIT_P_MAX || (unit_p & (unit_p - 1)) != 0)
+        return fail(b, PIC_ERR_INVALID_ARG, "unit size must be a power of two in [1024, 16384]");
+    if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 32]");
+    pic_status st = activate_pending(b);
+    if (st != PIC_OK) return st;
+    bool any = false;
+    for (auto& r : b->runs) any = any || (r.used && r.active);
+    if (unit_p != b->unit_p) {
+        // sort with the current table first (it also flushes the radiated
+        // partials), then rebuild the table from the sorted cells with the new size
+        if (any && b->since_sort > 0) do_sort(b);
+        const int64_t need = units_needed(b, unit_p);
+        if (need > (1 << 30)) return fail(b, PIC_ERR_INVALID_ARG, "too many work units");
+        if ((st = ensure_units(b, static_cast<int>(need))) != PIC_OK) return st;
+        b->unit_p = unit_p;
+        if (any) {
+            SortParams S = sort_params(b);
+            int nl = 0;
+            launch_build_units(S, b->stream, &nl);
+            b->launches += nl;
+        }
+    }
+    if (interval != b->sort_interval && b->since_sort > 0) do_sort(b);
+    b->sort_interval = interval;
+    b->epoch++;
+    return PIC_OK;
+}
+
+// Shape tuner: step the batch for a trial at each candidate work-unit size
+// (at the current sort interval), keep the fastest, then at each candidate
+// sort interval.  Each trial runs whole sort intervals as CUDA graphs after
+// one warm-up interval and measures the wall time per step.  The trial steps
+// are real steps of every active run; the shapes change only the order of
+// single-precision sums.
+pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval_out, double* ms_out) {
+    static const int units[4] = {2048, 4096, 8192, 16384};
+    static const int cand[4] = {4, 8, 16, 32};
+    if (steps_per < 1) return fail(b, PIC_ERR_INVALID_ARG, "steps_per_candidate must be >= 1");
+    if (b->timing) return fail(b, PIC_ERR_STATE, "turn timing off before tuning");
+    if (ms_out)
+        for (int i = 0; i < 8; ++i) ms_out[i] = -1.0;
+    auto trial = [&](int unit_p, int interval, double* per) -> pic_status {
+        *per = -1.0;
+        bool any = false;
+        for (auto& r : b->runs) any = any || (r.used && r.active);
+        if (!any) return PIC_OK;
+        pic_status st = set_shapes(b, unit_p, interval);
+        if (st != PIC_OK) return st;
+        int64_t done = 0;
+        if ((st = batch_step(b, interval, &done)) != PIC_OK) return st;  // captures the shape's graphs
+        if (done < interval) return PIC_OK;
+        const int64_t n = std::max<int64_t>(interval, steps_per / interval * interval);
+        const auto t0 = std::chrono::steady_clock::now();
+        if ((st = batch_step(b, n, &done)) != PIC_OK) return st;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (done == n) *per = ms / static_cast<double>(n);  // else a run ended inside the trial
+        return PIC_OK;
+    };
+    pic_status st = activate_pending(b);
+    if (st != PIC_OK) return st;
+    int best_u = b->unit_p, best_i = b->sort_interval;
+    double best = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        double per;
+        if ((st = trial(units[c], b->sort_interval, &per)) != PIC_OK) return st;
+        if (ms_out) ms_out[c] = per;
+        if (per > 0.0 && per < best) {
+            best = per;
+            best_u = units[c];
+        }
+    }
+    best = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        double per;
+        if ((st = trial(best_u, cand[c], &per)) != PIC_OK) return st;
+        if (ms_out) ms_out[4 + c] = per;
+        if (per > 0.0 && per < best) {
+            best = per;
+            best_i = cand[c];
+        }
+    }
+    if (best >= 1e300) return fail(b, PIC_ERR_STATE, "no active run stepped through a whole trial");
+    if ((st = set_shapes(b, best_u, best_i)) != PIC_OK) return st;
+    if (unit_out) *unit_out = best_u;
+    if (interval_out) *interval_out = best_i;
+    return PIC_OK;
+}
+
 // particle buffer and field buffer holding a run's current state
 int run_pbuf(const Batch* b, const RunHost& r) { return r.finished ? r.pbuf : b->cur; }
 int run_fbuf(const Batch* b, const RunHost& r) {
@@ -1227,6 +1336,96 @@ pic_status run_read_particles(Batch* b, int id, int species, int64_t cap, double
         if (py) py[j] = qy[i];
         if (pz) pz[j] = qz[i];
         if (flag) flag[j] = fl;
+    }
+    return PIC_OK;
+}
+
+// Skin-layer snapshot: d of Eq. (damping) and chi per particle on the device,
+// with their maxima and the count of chi >= chi_flag; per-particle values
+// (with x, p_x, p_perp) returned in load order when cap > 0.
+pic_status run_snapshot(Batch* b, int id, int species, double chi_flag, int64_t cap, double* x, double* px,
+                        double* pperp, double* d, double* chi, double* summary, int64_t* nout) {
+    if (species != PIC_ELECTRON && species != PIC_ION) return fail(b, PIC_ERR_INVALID_ARG, "bad species");
+    if (!(chi_flag >= 0.0) || !std::isfinite(chi_flag)) return fail(b, PIC_ERR_INVALID_ARG, "chi_flag must be >= 0");
+    const RunHost& r = b->runs[id];
+    const HostSpecies& h = r.sp[species];
+    const int64_t n = h.loaded ? h.n : 0;
+    if (nout) *nout = n;
+    if (summary) summary[0] = summary[1] = summary[2] = 0.0;
+    if (n == 0) return PIC_OK;
+    const bool per = cap > 0 && (x || px || pperp || d || chi);
+    std::vector<std::pair<void*, size_t>> tmp;
+    float *dd = nullptr, *dc = nullptr;
+    if (per) {
+        pic_status st = dalloc_t(b, tmp, &dd, static_cast<size_t>(n));
+        if (st == PIC_OK) st = dalloc_t(b, tmp, &dc, static_cast<size_t>(n));
+        if (st != PIC_OK) {
+            free_all(b, tmp);
+            return st;
+        }
+    }
+    SnapParams S{};
+    const int fb = run_fbuf(b, r);
+    for (int c = 0; c < 5; ++c) S.F[c] = r.dev.F[fb][c];
+    S.eps = static_cast<float>(b->eps);
+    S.ecr_inv = static_cast<float>(2.0 * kPi * kLambdaCUm / b->cfg.lambda_um);  // 1 / (m c^2 / hbar omega)
+    S.chi_flag = static_cast<float>(chi_flag);
+    const DevSpecies& sp = r.dev.sp[species][run_pbuf(b, r)];
+    PIC_CK(b, cudaMemsetAsync(b->snap_out, 0, 4 * sizeof(unsigned long long), b->stream));
+    launch_snapshot(sp, n, S, dd, dc, b->snap_out, b->stream);
+    b->launches++;
+    unsigned long long so[3];
+    PIC_CK(b, cudaMemcpyAsync(so, b->snap_out, sizeof(so), cudaMemcpyDeviceToHost, b->stream));
+    std::vector<int32_t> c, idv;
+    std::vector<float> o, qx, qy, qz, hd, hc;
+    if (per) {
+        c.resize(n);
+        idv.resize(n);
+        o.resize(n);
+        qx.resize(n);
+        qy.resize(n);
+        qz.resize(n);
+        hd.resize(n);
+        hc.resize(n);
+        const size_t by = static_cast<size_t>(n) * 4;
+        PIC_CK(b, cudaMemcpyAsync(c.data(), sp.cell, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(idv.data(), sp.id, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(o.data(), sp.off, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(qx.data(), sp.px, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(qy.data(), sp.py, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(qz.data(), sp.pz, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(hd.data(), dd, by, cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaMemcpyAsync(hc.data(), dc, by, cudaMemcpyDeviceToHost, b->stream));
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    free_all(b, tmp);
+    if (e != cudaSuccess) return cuda_fail(b, e, "snapshot");
+    if (summary) {
+        float f0, f1;
+        const unsigned int u0 = static_cast<unsigned int>(so[0]), u1 = static_cast<unsigned int>(so[1]);
+        std::memcpy(&f0, &u0, 4);
+        std::memcpy(&f1, &u1, 4);
+        summary[0] = f0;
+        summary[1] = f1;
+        summary[2] = static_cast<double>(so[2]);
+    }
+    if (!per) return PIC_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t j = idv[i];
+        if (j < 0 || j >= n) return fail(b, PIC_ERR_STATE, "corrupt particle id");
+        if (j >= cap) continue;
+        double xi;
+        if (c[i] < 0) {
+            const int key = -1 - c[i];
+            xi = key == 0 ? 0.0 : static_cast<double>(r.Nx);
+        } else {
+            xi = static_cast<double>(c[i]) + o[i];
+        }
+        if (x) x[j] = xi * b->dx;
+        if (px) px[j] = qx[i];
+        if (pperp) pperp[j] = std::sqrt(static_cast<double>(qy[i]) * qy[i] + static_cast<double>(qz[i]) * qz[i]);
+        if (d) d[j] = hd[i];
+        if (chi) chi[j] = hc[i];
     }
     return PIC_OK;
 }
@@ -1427,10 +1626,30 @@ pic_status pic_read_particles(pic_sim* s, int species, int64_t cap, double* x, d
     return run_read_particles(s->b, 0, species, cap, x, px, py, pz, flag, n);
 }
 
+pic_status pic_snapshot(pic_sim* s, int species, double chi_flag, int64_t cap, double* x, double* px, double* pperp,
+                        double* d, double* chi, double* summary, int64_t* n) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return run_snapshot(s->b, 0, species, chi_flag, cap, x, px, pperp, d, chi, summary, n);
+}
+
 pic_status pic_read_fields(pic_sim* s, int comp, int64_t cap, double* out, int64_t* n) {
     if (!s) return PIC_ERR_INVALID_ARG;
     DeviceGuard g(s->b->device);
     return run_read_fields(s->b, 0, comp, cap, out, n);
+}
+
+pic_status pic_tune_shapes(pic_sim* s, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
+                           double* ms_per_step) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return tune_shapes(s->b, steps_per_candidate, unit_particles, sort_interval, ms_per_step);
+}
+
+pic_status pic_set_shapes(pic_sim* s, int unit_particles, int sort_interval) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(s->b->device);
+    return set_shapes(s->b, unit_particles, sort_interval);
 }
 
 pic_status pic_stats(pic_sim* s, pic_stats_t* out) {
@@ -1563,6 +1782,14 @@ pic_status pic_batch_read_particles(pic_batch* h, int run, int species, int64_t 
     return run_read_particles(h->b, run, species, cap, x, px, py, pz, flag, n);
 }
 
+pic_status pic_batch_snapshot(pic_batch* h, int run, int species, double chi_flag, int64_t cap, double* x, double* px,
+                              double* pperp, double* d, double* chi, double* summary, int64_t* n) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    DeviceGuard g(h->b->device);
+    return run_snapshot(h->b, run, species, chi_flag, cap, x, px, pperp, d, chi, summary, n);
+}
+
 pic_status pic_batch_read_fields(pic_batch* h, int run, int comp, int64_t cap, double* out, int64_t* n) {
     pic_status st = check_run(h, run);
     if (st != PIC_OK) return st;
@@ -1578,6 +1805,19 @@ pic_status pic_batch_release_run(pic_batch* h, int run) {
     DeviceGuard g(b->device);
     run_release(b, run);
     return upload_table(b);
+}
+
+pic_status pic_batch_tune_shapes(pic_batch* h, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
+                                 double* ms_per_step) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(h->b->device);
+    return tune_shapes(h->b, steps_per_candidate, unit_particles, sort_interval, ms_per_step);
+}
+
+pic_status pic_batch_set_shapes(pic_batch* h, int unit_particles, int sort_interval) {
+    if (!h) return PIC_ERR_INVALID_ARG;
+    DeviceGuard g(h->b->device);
+    return set_shapes(h->b, unit_particles, sort_interval);
 }
 
 pic_status pic_batch_stats(pic_batch* h, pic_stats_t* out) {

@@ -23,17 +23,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "picrr.h"
 #include <stdint.h>
 
 namespace picrr {
 
 constexpr int PADF = 40;          // guard elements left of index 0 of every grid array
-constexpr int TILE = 64;          // cells per tile: bounds the cell span of a unit
-constexpr int UNIT_P = 2048;      // particles per unit at most
+constexpr int TILE = 64;          // cells per tile: a dense tile is split into units of at most unit_p particles
+constexpr int GROUP = 4;          // consecutive tiles that form one unit when they hold <= unit_p particles
+constexpr int SPAN = GROUP * TILE;  // cell span bound of a unit
+constexpr int UNIT_P = 4096;      // default particles per unit at most (unit_p, a run-time shape of a batch)
+constexpr int UNIT_P_MIN = 1024;  // smallest unit_p (the bound used for memory estimates)
+constexpr int UNIT_P_MAX = 16384;
 constexpr int KMAX = 32;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
-constexpr int WMAX = 144;         // window length bound in the push kernel (>= TILE + 2 KMAX + 10)
-constexpr int SSTR = TILE + 2 * KMAX + 4;  // per-unit key-window stride of the sort scratch
+constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push kernel (>= SPAN + 2 KMAX + 9)
+constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)
 constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
 constexpr int KEY_T = 256;        // cells per block of the per-cell sort kernels
 constexpr int NQ = 5;             // deposit quantities per bin: jy_lo, jy_hi, jz_lo, jz_hi, jx
@@ -182,6 +188,7 @@ struct SortParams {
     int* status;
     int k, cur, max_units;
     int kb_max;            // key blocks of the largest run: ceil(max Nx / 256)
+    int unit_p;            // particles per unit at most (UNIT_P_MIN..UNIT_P_MAX)
 };
 // Full re-sort of every active run (bounded displacement since the last sort)
 // and the new unit table; particles move from buffer cur to 1 - cur.
@@ -212,5 +219,19 @@ int launch_kinetic(DevSpecies sp, int64_t n, double* partials, int max_blocks, c
 void launch_reduce_partials(const double* partials, int n, double scale, double* out, cudaStream_t st);
 void launch_spectrum(DevSpecies sp, int64_t n, double mass_mev, int nbins, double e_min, double e_max,
                      unsigned long long* bins, cudaStream_t st);
+
+// Friction coefficient d (Eq. damping) and quantum parameter chi per particle
+// from the stored momentum and the fields at the particle.  d_out / chi_out
+// (nullable) in stored order; out[0], out[1]: float bits of max d and max chi
+// (atomicMax on the bits of non-negative floats); out[2]: count of chi >= chi_flag.
+struct SnapParams {
+    const float* F[5];
+    float eps, ecr_inv, chi_flag;
+};
+void launch_electron_scan(const pic_electron_case* cases, int64_t n, int integrator, int flags, double dt,
+                          int64_t nsteps, int every, double eps, double* out, int64_t nsamples, cudaStream_t st);
+
+void launch_snapshot(DevSpecies sp, int64_t n, const SnapParams& S, float* d_out, float* chi_out,
+                     unsigned long long* out, cudaStream_t st);
 
 }  // namespace picrr

@@ -1,6 +1,7 @@
 // Serving loop of the picrr C ABI: a worker thread that owns one batch,
-// admits queued run requests in arrival order as slots and the device-memory
-// budget allow, steps the batch in chunks (requests join between chunks while
+// admits queued run requests (in arrival order, or shortest work first) as
+// slots, the device-memory budget and an optional cap on resident particles
+// allow, steps the batch in chunks (requests join between chunks while
 // the others keep stepping), and turns every finished run into its spectra
 // and energy read-out before freeing it.  Built only on the public
 // pic_batch_* entry points; host code only.
@@ -37,6 +38,7 @@ struct Request {
     double ion_max = 0.0, el_max = 0.0;
     size_t footprint = 0;
     int64_t particles = 0;
+    double work = 0.0;  // particles x steps
     Clock::time_point submitted;
     ReqState state = QUEUED;
     int run = -1;
@@ -64,6 +66,9 @@ struct pic_server {
     int64_t next_ticket = 1;
     bool stop = false;
     pic_status fatal = PIC_OK;
+    int policy = PIC_SERVE_FIFO;
+    int64_t max_resident = 0;  // particles resident at once (0: no cap)
+    int64_t resident = 0;
     std::string fatal_msg;
     pic_server_stats_t st{};
     std::thread worker;
@@ -103,6 +108,7 @@ void pic_server::finish_run(Request* r) {
     const double lat = std::chrono::duration<double>(Clock::now() - r->submitted).count();
     std::lock_guard<std::mutex> lk(m);
     r->run = -1;
+    resident -= r->particles;
     st.running--;
     if (s == PIC_OK) {
         r->ion.swap(ion);
@@ -133,16 +139,24 @@ void pic_server::run() {
         {
             std::unique_lock<std::mutex> lk(m);
             if (stop) return;
-            // admission in arrival order: the head of the queue waits for room
+            // admission: the next request by the policy waits for room
             size_t used = static_cast<size_t>(bs.device_bytes);
             int free_slots = max_runs - static_cast<int>(running.size());
+            int64_t res = resident;
             while (!queue.empty() && free_slots > 0) {
-                Request* r = reqs[queue.front()].get();
-                // (with nothing resident, the head is admitted: it fits the budget alone)
-                if (budget && used + r->footprint > budget && !(running.empty() && admit.empty())) break;
-                queue.pop_front();
+                size_t pick = 0;
+                if (policy == PIC_SERVE_SHORTEST_FIRST)
+                    for (size_t q = 1; q < queue.size(); ++q)
+                        if (reqs[queue[q]]->work < reqs[queue[pick]]->work) pick = q;
+                Request* r = reqs[queue[pick]].get();
+                // (with nothing resident, the request is admitted: it fits the budget alone)
+                const bool alone = running.empty() && admit.empty();
+                if (budget && used + r->footprint > budget && !alone) break;
+                if (max_resident && res + r->particles > max_resident && !alone) break;
+                queue.erase(queue.begin() + static_cast<long>(pick));
                 admit.push_back(r);
                 used += r->footprint;
+                res += r->particles;
                 free_slots--;
             }
             st.queued = static_cast<int64_t>(queue.size());
@@ -156,6 +170,7 @@ void pic_server::run() {
                 r->run = id;
                 r->state = RUNNING;
                 running.push_back(r);
+                resident += r->particles;
                 st.admitted++;
                 st.running++;
             } else if (s == PIC_ERR_OOM && !running.empty()) {
@@ -252,6 +267,7 @@ pic_status pic_server_submit(pic_server* v, const pic_run_desc* d, int nbins, do
     r->el_max = el_e_max_MeV;
     r->footprint = fp;
     r->particles = 2 * static_cast<int64_t>(std::llround(d->foil_thickness_lambda * v->cells_per_lambda)) * d->ppc;
+    r->work = static_cast<double>(r->particles) * static_cast<double>(d->steps);
     r->submitted = Clock::now();
     std::lock_guard<std::mutex> lk(v->m);
     if (v->fatal != PIC_OK) return sfail(v->fatal, "server stopped: " + v->fatal_msg);
@@ -290,6 +306,18 @@ pic_status pic_server_result(pic_server* v, int64_t ticket, double wait_s, doubl
         for (int k = 0; k < 6; ++k) energy[k] = r->energy[k];
     if (latency_s) *latency_s = r->latency;
     v->reqs.erase(it);
+    return PIC_OK;
+}
+
+pic_status pic_server_set_policy(pic_server* v, int policy, int64_t max_resident_particles) {
+    if (!v) return sfail(PIC_ERR_INVALID_ARG, "server is NULL");
+    if (policy != PIC_SERVE_FIFO && policy != PIC_SERVE_SHORTEST_FIRST)
+        return sfail(PIC_ERR_INVALID_ARG, "unknown policy");
+    if (max_resident_particles < 0) return sfail(PIC_ERR_INVALID_ARG, "max_resident_particles must be >= 0");
+    std::lock_guard<std::mutex> lk(v->m);
+    v->policy = policy;
+    v->max_resident = max_resident_particles;
+    v->cv_work.notify_one();
     return PIC_OK;
 }
 

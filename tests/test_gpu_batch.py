@@ -207,3 +207,50 @@ def test_graph_chunks_equal_single_launches(picrr):
     assert st[0]["graph_launches"] == (d["steps"] - 8) // 8 and st[1]["graph_launches"] == 0
     assert st[0]["kernel_launches"] == st[1]["kernel_launches"]
     assert_same(out[0], out[1], "graph vs single launches")
+
+
+def test_shape_tuner(picrr):
+    """The tuner times real steps at unit sizes 2048..16384, then at sort
+    intervals 4..32, keeps the fastest pair, and the run stays on the same
+    trajectory up to rounding."""
+    d = EARLY  # the pulse is in the foil from step ~50 on
+    res = []
+    for tune in (True, False):
+        g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
+                      seed=d["seed"])
+        g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
+        if tune:
+            unit, interval, ms = g.tune_shapes(32)
+            assert unit in (2048, 4096, 8192, 16384) and interval in (4, 8, 16, 32) and np.all(ms > 0)
+            assert interval == (4, 8, 16, 32)[int(np.argmin(ms[4:]))]
+            done = g.stats()["steps"]
+            assert done == 4 * (8 + 32) + 4 + 32 + 8 + 32 + 16 + 32 + 32 + 32
+            g.step(400 - done)
+        else:
+            g.step(400)
+        res.append([g.field(c) for c in range(5)])
+        g.close()
+    for c in range(5):
+        assert np.linalg.norm(res[0][c] - res[1][c]) <= 1e-4 * max(np.linalg.norm(res[1][c]), 1e-30), c
+
+
+def test_set_shapes_changes_only_rounding(picrr):
+    d = EARLY
+    out = []
+    for unit, interval in ((1024, 8), (16384, 4), (4096, 16)):
+        g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
+                      seed=d["seed"])
+        g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
+        g.step(13)
+        g.set_shapes(unit, interval)  # mid-interval: sorted first
+        g.step(187)
+        out.append((np.concatenate([g.field(c) for c in range(5)]), g.particles(0)))
+        g.close()
+    for f, p in out[1:]:
+        assert np.linalg.norm(f - out[0][0]) <= 1e-5 * np.linalg.norm(out[0][0])
+        assert np.max(np.abs(p["px"] - out[0][1]["px"])) <= 1e-3 * (1 + np.max(np.abs(out[0][1]["px"])))
+    with pytest.raises(picrr.PicError):
+        g = picrr.Sim(length_lambda=4, cells_per_lambda=CPL)
+        g.set_shapes(3000, 8)

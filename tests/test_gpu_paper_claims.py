@@ -1,0 +1,84 @@
+"""The paper's qualitative claims (Sec. 4) on its own setup, stepped on the
+GPU: a hydrogen foil with n0 = 100 n_c, 1 wavelength thick, between 14 and 15
+wavelengths; a0 = 328 (2.33e23 W/cm^2 at 0.8 um) with the paper's
+trapezoidal envelope (one-cycle sin^2 rise and fall, five-cycle plateau), CP
+and LP, with and without RR; times counted from the arrival of the pulse
+front at the foil.  Grid lambda/1000, 100 macro-particles per cell per
+species (the paper's resolution is not given).  Claims checked:
+
+- CP: the friction coefficient d of Eq. (damping) in the skin layer is of
+  order 1e-2 at t = 1.7 T, the radiated energy is negligible and the ion
+  spectrum does not change with RR;
+- LP: d reaches about 1e2 at t = 1.6-1.7 T, up to four orders of magnitude
+  above CP; a sizeable fraction of the pulse energy is radiated (the paper
+  reports about 20 %); with RR the ion spectrum at 12 T has a lower peak
+  energy and a smaller spread.
+
+The bands are wide on purpose: the claims are qualitative, and the paper's
+grid, particle numbers and diagnostics are not given.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+CPL, PPC, X0 = 1000, 100, 14.0
+A0 = 328.0
+U_PULSE = 0.5 * A0 ** 2 * 2 * math.pi * (5 + 0.75)  # integral of the incident Poynting flux, trapezoid 1-5-1
+
+
+@pytest.fixture(scope="module")
+def runs():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1008_1685_gb300 as picrr
+
+    out = {}
+    for pol, name in ((picrr.CP, "CP"), (picrr.LP, "LP")):
+        for rr in (True, False):
+            g = picrr.Sim(20.0, CPL, rr_on=rr, sort_interval=8, seed=5)
+            g.load_foil(X0, 1.0, 100.0, 1, 1.0, PPC)
+            g.inject_laser(A0, pol, picrr.ENV_TRAPEZOID, 7.0, 1.0)
+            t_arrival = X0 * 2 * math.pi - 8 * g.dx  # the front leaves the source node at t = 0
+            rec, done = {}, 0
+            for tag, periods in (("1.6", 1.6), ("1.7", 1.7), ("12", 12.0), ("30", 30.0)):
+                n = int(round((t_arrival + periods * 2 * math.pi) / g.dt)) - done
+                done += g.step(n)
+                r = dict(energy=g.energy())
+                if tag in ("1.6", "1.7"):
+                    r["snap"] = g.snapshot(0, chi_flag=0.1)
+                if tag == "12":
+                    c, _ = g.spectra(1, 400, 0.0, 4000.0)
+                    e = (np.arange(400) + 0.5) * 10.0
+                    sm = np.convolve(c, np.ones(9) / 9, "same")
+                    mean = c @ e / c.sum()
+                    r["ion"] = dict(peak=e[np.argmax(sm)], mean=mean, std=math.sqrt(c @ (e - mean) ** 2 / c.sum()))
+                rec[tag] = r
+            g.close()
+            out[name + ("_RR" if rr else "_noRR")] = rec
+    return out
+
+
+def test_cp_friction_small_and_rr_negligible(runs):
+    cp = runs["CP_RR"]
+    d = cp["1.7"]["snap"]["d"]
+    assert 1e-3 < np.percentile(d, 99) < 1e-1  # "d ~ 1e-2" in the skin layer
+    assert cp["1.7"]["snap"]["d_max"] < 0.3
+    assert cp["30"]["energy"][3] < 1e-3 * U_PULSE  # radiated energy negligible
+    a, b = cp["12"]["ion"], runs["CP_noRR"]["12"]["ion"]
+    assert a["peak"] == pytest.approx(b["peak"], rel=0.02) and a["mean"] == pytest.approx(b["mean"], rel=0.02)
+
+
+def test_lp_friction_large_and_rr_matters(runs):
+    lp = runs["LP_RR"]
+    dmax = max(lp["1.6"]["snap"]["d_max"], lp["1.7"]["snap"]["d_max"])
+    assert 30.0 < dmax < 1000.0  # "d of about 1e2, comparable with a0"
+    cp_max = max(runs["CP_RR"]["1.6"]["snap"]["d_max"], runs["CP_RR"]["1.7"]["snap"]["d_max"])
+    assert dmax / cp_max > 1e3  # "up to four orders of magnitude"
+    frac = lp["30"]["energy"][3] / U_PULSE
+    assert 0.05 < frac < 0.4  # "about 20 % of the pulse energy lost as incoherent radiation"
+    a, b = lp["12"]["ion"], runs["LP_noRR"]["12"]["ion"]
+    assert a["peak"] < b["peak"]  # lower peak energy with RR
+    assert a["std"] < b["std"]  # smaller spread with RR

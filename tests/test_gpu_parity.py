@@ -3,8 +3,9 @@ the same seeded inputs.  Tolerances (single-precision particles and fields):
   - momenta after one step: per particle, max-norm difference <= 1e-5 of
     max(|p|, 1e-3 F dt), F the field scale;
   - fields after 200 steps: relative L2 per component <= 1e-4;
-  - full runs: ion spectrum peak and FWHM within 2 %, energy bookkeeping
-    within 1e-3 of the injected energy.
+  - full runs (tests/test_gpu_fullrun.py): energy bookkeeping within 1e-3 of
+    the injected energy; ion spectra compared as 1024-seed ensembles (full
+    runs are chaotic): peak, FWHM and mean energy within 2 %.
 """
 import math
 

@@ -110,3 +110,36 @@ def test_unknown_ticket_and_poll(picrr):
     with pytest.raises(KeyError):
         srv.result(t)
     srv.close()
+
+
+@pytest.mark.parametrize("policy", ["fifo", "sjf"])
+def test_admission_order_policy(picrr, policy):
+    """One run resident at a time (particle cap); while the first request runs,
+    a medium and then a small request queue up.  Arrival order serves the
+    medium one first, least-work-first the small one."""
+    big = dict(RUNS[1], seed=31)                    # admitted at once, runs while the others queue
+    medium = dict(RUNS[0], seed=32)                 # 1200 particles per species, 704 steps
+    small = dict(RUNS[2], seed=33, steps=300)       # 480 particles per species, 300 steps
+    srv = picrr.Server(CPL, max_runs=3, chunk_steps=32)
+    # room for the medium run, not for medium + small; the big run is admitted alone
+    cap = 2 * medium["ppc"] * round(medium["foil_thickness"] * CPL)
+    srv.set_policy(picrr.SERVE_SHORTEST_FIRST if policy == "sjf" else picrr.SERVE_FIFO, cap)
+    kw = dict(nbins=NB, ion_e_max=ION_MAX, el_e_max=EL_MAX)
+    tb = srv.submit(**kw, **desc(big))
+    t0 = time.time()
+    while srv.stats()["running"] < 1 and time.time() - t0 < 60:
+        time.sleep(0.001)
+    tm = srv.submit(**kw, **desc(medium))
+    ts = srv.submit(**kw, **desc(small))
+    rb, rm, rs = (srv.result(t, wait_s=300.0) for t in (tb, tm, ts))
+    st = srv.stats()
+    assert st["completed"] == 3
+    # one at a time: the batch steps add up
+    assert st["batch_steps"] == big["steps"] + medium["steps"] + small["steps"]
+    if policy == "sjf":
+        assert rs["latency_s"] < rm["latency_s"]
+    else:
+        assert rm["latency_s"] < rs["latency_s"]
+    for res, d in ((rb, big), (rm, medium), (rs, small)):
+        assert_same(res, solo(picrr, d), d["seed"])
+    srv.close()
