@@ -40,6 +40,11 @@ LARGE = dict(length_lambda=100.0, cells_per_lambda=2000.0, cfl=0.95, lambda_um=0
              source_node=8, foil_x0=0.25, foil_thickness=2.0, ne=100.0, ppc=8000, a0=500.0, pol=1,
              duration=20.0, seed=4, sort_interval=8)
 BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int32 + 4 x fp32)
+# DRAM traffic of one push launch of this workload, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles,
+# 16384 particles per unit, sort every 32 steps); reported when the run matches
+PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=32,
+                    bytes=1_280_281_856 + 1_219_174_912)
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
@@ -71,8 +76,10 @@ def desc_particles(d, cpl):
 # the served request stream: Poisson arrivals, sizes log-uniform in 1e4..1e6
 # particles per species, 20..200 periods, physical parameters as in the scan,
 # admission by device memory under a 150 GB budget
-SERVE = dict(rate=20.0, window_s=10.0, cap_s=45.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77,
+SERVE = dict(rate=20.0, window_s=10.0, cap_s=40.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77,
              policy="sjf", resident=24_000_000)
+# a second stream at a rate one GB300 keeps up with for this mix (its capacity is about 1 request/s)
+SERVE_LOW = dict(SERVE, rate=0.5, window_s=20.0, cap_s=40.0)
 
 
 def serve_requests(rate, window_s, seed, w=SCAN):
@@ -188,10 +195,13 @@ def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
     return _latency_summary(lat, [el - reqs[j][0] for j in pending if reqs[j][0] <= el], el, len(reqs))
 
 
-def batched_scan(picrr, device, n_runs, w=SCAN):
+def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None):
     """All runs in one batch (one launch per kernel per step for all of them),
-    from creation to every run's ion spectrum on the host."""
+    from creation to every run's ion spectrum on the host.  max_steps (for
+    profiling) cuts every run short."""
     descs = [scan_desc(i, w) for i in range(n_runs)]
+    if max_steps:
+        descs = [dict(d, steps=min(d["steps"], max_steps)) for d in descs]
     t0 = time.perf_counter()
     b = picrr.Batch(w["cells_per_lambda"], max_runs=n_runs, cfl=w["cfl"], sort_interval=w["sort_interval"],
                     device=device)
@@ -398,12 +408,15 @@ def main():
     ap.add_argument("--shapes", default=None,
                     help="UNIT,INTERVAL: set these launch shapes instead of running the tuner (profiling)")
     ap.add_argument("--scan-runs", type=int, default=SCAN["n_runs"], help="runs of the batched scan (0: skip)")
+    ap.add_argument("--scan-steps", type=int, default=0, help="cut the scan runs to this many steps (profiling)")
     ap.add_argument("--plain-runs", type=int, default=8,
                     help="runs of the scan stepped one at a time for the plain comparison (0: skip)")
     ap.add_argument("--serve-window", type=float, default=SERVE["window_s"],
                     help="seconds of request arrivals of the serving leg (0: skip)")
     ap.add_argument("--serve-cap", type=float, default=SERVE["cap_s"], help="time cap of each serving arm (s)")
     ap.add_argument("--serve-rate", type=float, default=SERVE["rate"], help="request arrivals per second")
+    ap.add_argument("--serve-low-rate", type=float, default=SERVE_LOW["rate"],
+                    help="arrival rate of the second (sustainable) stream; 0 skips it")
     ap.add_argument("--serve-policy", default=SERVE["policy"], choices=["sjf", "fifo"],
                     help="admission order of both serving arms: least work first, or arrival order")
     ap.add_argument("--serve-resident", type=int, default=SERVE["resident"],
@@ -482,6 +495,10 @@ def main():
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_PARTICLE_STEP * n_active / (push_avg_ms / 1e3) / 1e9
     launches = st1["kernel_launches"] - st0["kernel_launches"]
+    traffic = None
+    if (shapes and n_active == PUSH_TRAFFIC["particles"] and shapes["unit_particles"] == PUSH_TRAFFIC["unit_particles"]
+            and shapes["sort_interval"] == PUSH_TRAFFIC["sort_interval"]):
+        traffic = PUSH_TRAFFIC["bytes"]
     sim.close()
 
     e2e = None
@@ -496,7 +513,7 @@ def main():
 
     scan = None
     if args.scan_runs > 0:
-        scan = batched_scan(picrr, local, args.scan_runs)
+        scan = batched_scan(picrr, local, args.scan_runs, max_steps=args.scan_steps or None)
         if args.plain_runs > 0:
             plain = plain_scan(picrr, local, min(args.plain_runs, args.scan_runs))
             scan["plain"] = plain
@@ -509,19 +526,27 @@ def main():
 
     serving = None
     if args.serve_window > 0:
-        cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
-                   policy=args.serve_policy, resident=args.serve_resident)
-        serving = serve_leg(picrr, local, cfg)
-        serving["plain"] = plain_serve_leg(picrr, local, cfg)
-        serving["overloaded"] = serving["offered_particle_steps_per_s"] > serving["served_particle_steps_per_s"]
-        serving["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
+        def one_stream(cfg):
+            out = serve_leg(picrr, local, cfg)
+            out["plain"] = plain_serve_leg(picrr, local, cfg)
+            out["overloaded"] = out["offered_particle_steps_per_s"] > out["served_particle_steps_per_s"]
+            out["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
                                "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
-                               "the scan; 150 GB admission budget, %d slots, at most %d particles stepping at once, %d-step "
-                               "chunks, admission %s in both arms; each arm capped at %g s; latency = submission "
-                               "to ion + electron spectra on the host"
+                               "the scan; 150 GB admission budget, %d slots, at most %d particles stepping at once, "
+                               "%d-step chunks, admission %s in both arms; each arm capped at %g s; latency = "
+                               "submission to ion + electron spectra on the host"
                                % (cfg["rate"], cfg["window_s"], cfg["seed"], cfg["max_runs"], cfg["resident"],
                                   cfg["chunk"], "least work first" if cfg["policy"] == "sjf" else "in arrival order",
                                   cfg["cap_s"]))
+            return out
+
+        cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
+                   policy=args.serve_policy, resident=args.serve_resident)
+        serving = one_stream(cfg)
+        if args.serve_low_rate > 0:
+            low = dict(SERVE_LOW, cap_s=args.serve_cap, rate=args.serve_low_rate, policy=args.serve_policy,
+                       resident=args.serve_resident)
+            serving["sustainable_rate"] = one_stream(low)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -541,7 +566,7 @@ def main():
                        "l2": "inputs larger than L2: 2.56 GB particle state streamed per step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_push_deposit", "kernel_ms": push_avg_ms,
                          "peak_kind": peak_kind,
                          "bytes_per_launch": BYTES_PER_PARTICLE_STEP * n_active},

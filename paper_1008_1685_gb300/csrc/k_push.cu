@@ -3,26 +3,27 @@
 //
 // One CTA per work unit (at most unit_p consecutive particles of one species
 // whose cells at the last sort lie in one tile, or in one group of sparse
-// tiles holding at most unit_p particles; unit_p is a shape of the batch).  Because cfl < 1 a particle
-// moves less than one cell per step, so k steps after the sort every
-// particle of the unit lies in [lo - k, hi + k]; the CTA stages the fields of
-// the window [lo - k - 1, hi + k + 2] into shared memory with one bulk TMA
-// copy per component (completing on one mbarrier), streams the particles
-// (structure of arrays) with 128-bit evict-first loads and stores, and
-// accumulates the unit's current in shared memory.
+// tiles holding at most unit_p particles; unit_p is a shape of the batch).
+// Because cfl < 1 a particle moves less than one cell per step, so k steps
+// after the sort every particle of the unit lies in [lo - k, hi + k]; the CTA
+// stages the fields of the window [lo - k - 1, hi + k + 2] into shared memory
+// with one bulk TMA copy per component (completing on one mbarrier), streams
+// the particles (structure of arrays) with 128-bit evict-first loads and
+// stores, and accumulates the unit's current in shared memory.
 //
-// Determinism: each particle's current is split into at most two "bin"
-// records (its old cell and, if it crossed a boundary, its new cell), each
-// with five values (Jy and Jz shares of the bin's two nodes, and the Jx of
-// the bin's half node).  A thread first adds the old-bin records of its
-// successive particles that share a bin, in a fixed order; the
-// record is then converted to a 32-bit fixed-point value and the lanes of a
-// warp holding the same bin are summed exactly with an integer warp
-// reduction (match + reduce), whose total is shifted to the 64-bit scale of
-// the accumulators and added with one integer atomic per value, first into
-// shared memory, then into global memory.  Integer addition is exact and
-// associative, so the result does not depend on the order in which lanes,
-// warps or CTAs arrive.
+// Deposit: a particle that moves from bin b (cell at x^n) to bin b + d,
+// d in {-1, 0, 1}, touches Jy and Jz on at most three nodes and Jx on at most
+// two half nodes, all within the stencil anchored at a = min(b, b + d): one
+// record of eight values per particle (the 1D Esirkepov split for linear
+// shapes: the old bin's share up to the crossing point, the new bin's after
+// it).  Determinism: a thread first adds the records of its successive
+// particles that share an anchor, in a fixed order; the record is then
+// converted to 32-bit fixed point and the lanes of a warp holding the same
+// anchor are summed exactly with an integer warp reduction (match + reduce),
+// whose total is shifted to the 64-bit scale of the accumulators and added
+// with one integer atomic per value, first into shared memory, then into
+// global memory.  Integer addition is exact and associative, so the result
+// does not depend on the order in which lanes, warps or CTAs arrive.
 #include "picrr_internal.cuh"
 
 namespace picrr {
@@ -31,25 +32,26 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Add one bin record per lane to sJ[q][key]: lanes with equal keys are
-// summed exactly in 32-bit fixed point (2^lscale units, |value| < 2^26 per
-// lane), the sum is shifted to the accumulators' 2^fp units and added by the
-// group's first lane.  key < 0 marks an empty record.
-__device__ __forceinline__ void warp_add(int key, float v0, float v1, float v2, float v3, float v4,
-                                         unsigned long long (*sJ)[WMAX], float lscale, int shift) {
+// Add one stencil record per lane: lanes with equal anchors are summed
+// exactly in 32-bit fixed point (2^lscale units, |value| < 2^26 per lane), the
+// sums are shifted to the accumulators' 2^fp units and added by the group's
+// first lane to Jy and Jz on nodes key..key+2 and Jx on half nodes key, key+1.
+// key < 0 marks an empty record.
+__device__ __forceinline__ void warp_add(int key, const float (&v)[8], unsigned long long (*sJ)[WMAX], float lscale,
+                                         int shift) {
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(FULL, key);
-    const int s0 = __reduce_add_sync(peers, __float2int_rn(v0 * lscale));
-    const int s1 = __reduce_add_sync(peers, __float2int_rn(v1 * lscale));
-    const int s2 = __reduce_add_sync(peers, __float2int_rn(v2 * lscale));
-    const int s3 = __reduce_add_sync(peers, __float2int_rn(v3 * lscale));
-    const int s4 = __reduce_add_sync(peers, __float2int_rn(v4 * lscale));
+    int t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t[q] = __reduce_add_sync(peers, __float2int_rn(v[q] * lscale));
     if (key >= 0 && lane == __ffs(peers) - 1) {
-        if (s0) atomicAdd(&sJ[0][key], static_cast<unsigned long long>(static_cast<long long>(s0) << shift));
-        if (s1) atomicAdd(&sJ[1][key], static_cast<unsigned long long>(static_cast<long long>(s1) << shift));
-        if (s2) atomicAdd(&sJ[2][key], static_cast<unsigned long long>(static_cast<long long>(s2) << shift));
-        if (s3) atomicAdd(&sJ[3][key], static_cast<unsigned long long>(static_cast<long long>(s3) << shift));
-        if (s4) atomicAdd(&sJ[4][key], static_cast<unsigned long long>(static_cast<long long>(s4) << shift));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            // q 0..2: Jy at key+q; 3..5: Jz at key+q-3; 6, 7: Jx at key, key+1
+            const int comp = q < 3 ? 1 : (q < 6 ? 2 : 0);
+            const int at = key + (q < 3 ? q : (q < 6 ? q - 3 : q - 6));
+            if (t[q]) atomicAdd(&sJ[comp][at], static_cast<unsigned long long>(static_cast<long long>(t[q]) << shift));
+        }
     }
 }
 
@@ -60,7 +62,7 @@ __device__ __forceinline__ float comp(const float4& a, int j) {
 
 __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) {
     __shared__ __align__(128) float sF[5][WMAX];
-    __shared__ __align__(16) unsigned long long sJ[NQ][WMAX];
+    __shared__ __align__(16) unsigned long long sJ[3][WMAX];  // Jx (half nodes), Jy, Jz (nodes) of the window
     __shared__ __align__(8) uint64_t bar;
     __shared__ double sred[PUSH_T / 32];
 
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
         return;
     }
 
-    for (int i = tid; i < NQ * WMAX; i += PUSH_T) (&sJ[0][0])[i] = 0ull;
+    for (int i = tid; i < 3 * WMAX; i += PUSH_T) (&sJ[0][0])[i] = 0ull;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -123,8 +125,8 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
     }
 
     float rad = 0.f;
-    int rk = -1;  // running old-bin record of this thread
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, r4 = 0.f;
+    int rk = -1;  // running stencil record of this thread (anchor rk)
+    float rv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 
     for (int r = 0; r < rounds; ++r) {
         const int slot = r * PUSH_T + tid;
@@ -154,9 +156,8 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
                 atomicOr(P.status, ST_WINDOW);
                 a = false;
             }
-            int ko = -1, kn = -1;
-            float vo0 = 0.f, vo1 = 0.f, vo2 = 0.f, vo3 = 0.f, vo4 = 0.f;
-            float vn0 = 0.f, vn1 = 0.f, vn2 = 0.f, vn3 = 0.f, vn4 = 0.f;
+            int ka = -1;  // anchor of this particle's stencil record
+            float pv[8];
             if (a) {
                 // --- linear gather: nodes (Ey, Ez) and half nodes (Ex, By, Bz)
                 const float e_y = (1.f - f) * sF[1][lb] + f * sF[1][lb + 1];
@@ -232,44 +233,43 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
                 }
                 // --- deposit records (old bin lb, new bin lb + d)
                 const float ay = 0.5f * qw * vyn, az = 0.5f * qw * vzn;
-                ko = lb;
+                // --- stencil record anchored at a = min(old bin, new bin): Jy, Jz on
+                // nodes a..a+2 and Jx on half nodes a, a+1 (Esirkepov for linear shapes)
                 {
-                    const bool cross = d != 0;
                     const float g0 = 1.f - f, g1 = 1.f - fn;
-                    const float wlo = cross ? g0 : g0 + g1, whi = cross ? f : f + fn;
-                    vo0 = ay * wlo;
-                    vo1 = ay * whi;
-                    vo2 = az * wlo;
-                    vo3 = az * whi;
-                    vo4 = cross ? (d > 0 ? jxf * g0 : -jxf * f) : jxf * (fn - f);
-                    kn = cross ? lb + d : -1;
-                    vn0 = ay * g1;
-                    vn1 = ay * fn;
-                    vn2 = az * g1;
-                    vn3 = az * fn;
-                    vn4 = d > 0 ? jxf * fn : -jxf * g1;
+                    const bool up = d > 0, down = d < 0;
+                    ka = down ? lb - 1 : lb;
+                    // node weights (time-averaged shape, doubled): old bin [lb, lb+1], new bin [lb+d, lb+d+1]
+                    const float w0 = down ? g1 : g0 + (up ? 0.f : g1);
+                    const float w1 = down ? fn + g0 : (up ? f + g1 : f + fn);
+                    const float w2 = down ? f : (up ? fn : 0.f);
+                    pv[0] = ay * w0;
+                    pv[1] = ay * w1;
+                    pv[2] = ay * w2;
+                    pv[3] = az * w0;
+                    pv[4] = az * w1;
+                    pv[5] = az * w2;
+                    pv[6] = up ? jxf * g0 : (down ? -jxf * g1 : jxf * (fn - f));
+                    pv[7] = up ? jxf * fn : (down ? -jxf * f : 0.f);
                 }
                 c = store_c;
                 f = fn;
             }
-            // merge the old-bin record into this thread's running record
-            const bool merge = ko < 0 || rk < 0 || ko == rk;
+            // merge the particle's record into this thread's running record
+            const bool merge = ka < 0 || rk < 0 || ka == rk;
             if (__any_sync(FULL, !merge)) {
-                warp_add(merge ? -1 : rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
+                warp_add(merge ? -1 : rk, rv, sJ, lscale, shift);
                 if (!merge) {
                     rk = -1;
-                    r0 = r1 = r2 = r3 = r4 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) rv[q] = 0.f;
                 }
             }
-            if (ko >= 0) {
-                rk = ko;
-                r0 += vo0;
-                r1 += vo1;
-                r2 += vo2;
-                r3 += vo3;
-                r4 += vo4;
+            if (ka >= 0) {
+                rk = ka;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) rv[q] += pv[q];
             }
-            if (__any_sync(FULL, kn >= 0)) warp_add(kn, vn0, vn1, vn2, vn3, vn4, sJ, lscale, shift);
             act[j] = a;
             cn[j] = c;
             fo[j] = f;
@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
             qy[j] = py;
             qz[j] = pz;
         }
-        warp_add(rk, r0, r1, r2, r3, r4, sJ, lscale, shift);
+        warp_add(rk, rv, sJ, lscale, shift);
         rk = -1;
-        r0 = r1 = r2 = r3 = r4 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rv[q] = 0.f;
         if (slot_ok) {
             if (b4 >= start && b4 + 3 < end) {
                 __stcs(reinterpret_cast<int4*>(sp.cell + b4), make_int4(cn[0], cn[1], cn[2], cn[3]));
@@ -313,11 +314,9 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
         for (int w = 0; w < PUSH_T / 32; ++w) t += sred[w];
         P.rad_part[u] += t * static_cast<double>(R.rad_w[s]);  // summed into the tally at the next flush
     }
-    // flush the window: node n gets jy_lo of bin n and jy_hi of bin n-1
+    // flush the window
     for (int i = tid; i < L; i += PUSH_T) {
-        const unsigned long long jy = sJ[0][i] + (i > 0 ? sJ[1][i - 1] : 0ull);
-        const unsigned long long jz = sJ[2][i] + (i > 0 ? sJ[3][i - 1] : 0ull);
-        const unsigned long long jx = sJ[4][i];
+        const unsigned long long jx = sJ[0][i], jy = sJ[1][i], jz = sJ[2][i];
         if (jx) atomicAdd(R.J[par][0] + p0 + i, jx);
         if (jy) atomicAdd(R.J[par][1] + p0 + i, jy);
         if (jz) atomicAdd(R.J[par][2] + p0 + i, jz);

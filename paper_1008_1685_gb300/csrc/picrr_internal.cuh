@@ -42,7 +42,6 @@ constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push k
 constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)
 constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
 constexpr int KEY_T = 256;        // cells per block of the per-cell sort kernels
-constexpr int NQ = 5;             // deposit quantities per bin: jy_lo, jy_hi, jz_lo, jz_hi, jx
 constexpr int WAIT_LIMIT = 1 << 22;  // bounded spin on an mbarrier before reporting a timeout
 
 // Device status bits (pic_step_n reads them after each call).
