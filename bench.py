@@ -529,7 +529,7 @@ def main():
         def one_stream(cfg):
             out = serve_leg(picrr, local, cfg)
             out["plain"] = plain_serve_leg(picrr, local, cfg)
-            out["overloaded"] = out["offered_particle_steps_per_s"] > out["served_particle_steps_per_s"]
+            out["overloaded"] = out["unfinished"] > 0  # the queue had not drained when the cap ended the arm
             out["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
                                "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
                                "the scan; 150 GB admission budget, %d slots, at most %d particles stepping at once, "

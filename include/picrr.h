@@ -233,6 +233,15 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything; NULL is accepted. */
 pic_status pic_destroy(pic_sim* sim);
 
+/* Self-test of failure detection on the device: launches one small kernel
+ * whose mbarrier wait can never complete (it expects two arrivals and gets
+ * one).  The wait is the bounded one every kernel of this library uses; it
+ * gives up after its fixed number of polls, the kernel records the timeout in
+ * a status word and the call returns PIC_ERR_TIMEOUT, with the CUDA context
+ * still usable.  *seconds (nullable) receives the wall time it took.  No
+ * trap, fault or unbounded wait is involved. */
+pic_status pic_selftest_wait_timeout(int device, double* seconds);
+
 /* ---- Batches of independent runs ---------------------------------------------
  * A batch steps many independent runs together: every kernel of a step is
  * one launch for all active runs of the batch, so small runs share the GPU
@@ -286,7 +295,10 @@ pic_status pic_batch_read_fields(pic_batch* batch, int run, int comp, int64_t ca
 /* As pic_snapshot, for one run of the batch. */
 pic_status pic_batch_snapshot(pic_batch* batch, int run, int species, double chi_flag, int64_t cap, double* x,
                               double* px, double* pperp, double* d, double* chi, double* summary, int64_t* n);
-/* Free a finished run's device memory; its slot can take a new run. */
+/* Stop a run before its step count (between steps): it leaves the batch at
+ * its current step, and its state stays readable until released. */
+pic_status pic_batch_stop_run(pic_batch* batch, int run);
+/* Free a finished, stopped or not yet started run's device memory; its slot can take a new run. */
 pic_status pic_batch_release_run(pic_batch* batch, int run);
 /* Device bytes the run described by desc would take in this batch: its grid,
  * sort scratch and both particle buffers, plus its share of the batch's work
@@ -355,6 +367,11 @@ pic_status pic_server_result(pic_server* srv, int64_t ticket, double wait_s, dou
 enum { PIC_SERVE_FIFO = 0, PIC_SERVE_SHORTEST_FIRST = 1 };
 pic_status pic_server_set_policy(pic_server* srv, int policy, int64_t max_resident_particles);
 pic_status pic_server_stats(pic_server* srv, pic_server_stats_t* out);
+/* Cancel a request: a queued one is dropped at once; a running one leaves the
+ * batch at the end of the current step chunk and its memory is freed.  Its
+ * result then reports PIC_ERR_STATE ("cancelled").  PIC_ERR_STATE if it has
+ * already finished; PIC_ERR_INVALID_ARG for an unknown ticket. */
+pic_status pic_server_cancel(pic_server* srv, int64_t ticket);
 /* Message of the last failed server call of the calling thread. */
 const char* pic_server_last_error(const pic_server* srv);
 /* Stop the worker (unfinished requests are dropped) and free everything. */

@@ -35,7 +35,7 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_server_last_error", "pic_server_destroy", "pic_tune_shapes",
            "pic_batch_tune_shapes", "pic_set_shapes", "pic_batch_set_shapes", "pic_server_set_policy",
            "pic_snapshot", "pic_batch_snapshot",
-           "pic_electron_scan")
+           "pic_electron_scan", "pic_selftest_wait_timeout", "pic_batch_stop_run", "pic_server_cancel")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -190,6 +190,9 @@ def library():
         L.pic_server_set_policy.argtypes = [vp, C.c_int, i64]
         L.pic_electron_scan.argtypes = [C.POINTER(ElectronCase), i64, C.c_int, C.c_int, C.c_double, i64, C.c_int,
                                         C.c_double, C.c_int, dp, i64]
+        L.pic_selftest_wait_timeout.argtypes = [C.c_int, dp]
+        L.pic_batch_stop_run.argtypes = [vp, C.c_int]
+        L.pic_server_cancel.argtypes = [vp, i64]
         L.pic_snapshot.argtypes = [vp, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp, C.POINTER(i64)]
         L.pic_batch_snapshot.argtypes = [vp, C.c_int, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp,
                                          C.POINTER(i64)]
@@ -198,6 +201,14 @@ def library():
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
+
+
+def selftest_wait_timeout(device=0):
+    """Run the device wait self-test; returns (status, seconds).  The expected
+    status is -5 (PIC_ERR_TIMEOUT): the bounded wait gave up."""
+    sec = C.c_double(0.0)
+    rc = library().pic_selftest_wait_timeout(device, C.byref(sec))
+    return rc, sec.value
 
 
 def electron_scan(cases, integrator=INTEGRATOR_RK4, rr=True, deriv=False, dt=0.01, nsteps=1000, every=1,
@@ -489,6 +500,9 @@ class Batch:
             raise PicError(rc, self._L.pic_batch_last_error(None).decode())
         return out.value
 
+    def stop_run(self, run):
+        self._check(self._L.pic_batch_stop_run(self._h, run))
+
     def release_run(self, run):
         self._check(self._L.pic_batch_release_run(self._h, run))
 
@@ -563,6 +577,11 @@ class Server:
 
     def set_policy(self, policy=SERVE_FIFO, max_resident_particles=0):
         rc = self._L.pic_server_set_policy(self._h, policy, max_resident_particles)
+        if rc != 0:
+            raise self._err(rc)
+
+    def cancel(self, ticket):
+        rc = self._L.pic_server_cancel(self._h, ticket)
         if rc != 0:
             raise self._err(rc)
 

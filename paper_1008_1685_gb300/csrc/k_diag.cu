@@ -153,7 +153,53 @@ __global__ void __launch_bounds__(DIAG_T) k_snapshot(DevSpecies sp, int64_t n, c
     }
 }
 
+// Checks of an uploaded particle array: out[0] counts cells outside [0, Nx),
+// out[1] offsets outside [0, 1) or non-finite momenta, out[2] places where the
+// cells decrease (the array is not in cell order).
+__global__ void __launch_bounds__(DIAG_T) k_validate(const int32_t* cell, const float* off, const float* px,
+                                                     const float* py, const float* pz, int64_t n, int Nx,
+                                                     unsigned long long* out) {
+    unsigned long long bad_cell = 0, bad_val = 0, down = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * DIAG_T + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * DIAG_T) {
+        const int c = cell[i];
+        const float f = off[i];
+        bad_cell += (c < 0 || c >= Nx) ? 1 : 0;
+        bad_val += (!(f >= 0.f && f < 1.f) || !isfinite(px[i]) || !isfinite(py[i]) || !isfinite(pz[i])) ? 1 : 0;
+        down += (i > 0 && c < cell[i - 1]) ? 1 : 0;
+    }
+    if (bad_cell) atomicAdd(&out[0], bad_cell);
+    if (bad_val) atomicAdd(&out[1], bad_val);
+    if (down) atomicAdd(&out[2], down);
+}
+
+// Self-test of the bounded device wait: an mbarrier that expects two
+// arrivals gets one, so its phase never completes; the wait (the helper the
+// push kernel uses for its field window) gives up after its bounded number of
+// polls and the kernel records the timeout in the status word.
+__global__ void k_wait_selftest(int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_arrive(&bar);
+    const bool got = mbar_wait_bounded(&bar, 0);
+    if (!__syncthreads_and(got) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
 }  // namespace
+
+void launch_wait_selftest(int* status, cudaStream_t st) { k_wait_selftest<<<1, 32, 0, st>>>(status); }
+
+void launch_validate(const int32_t* cell, const float* off, const float* px, const float* py, const float* pz,
+                     int64_t n, int Nx, unsigned long long* out, cudaStream_t st) {
+    int64_t g = (n + DIAG_T - 1) / DIAG_T;
+    if (g > 4864) g = 4864;
+    if (g < 1) g = 1;
+    k_validate<<<static_cast<int>(g), DIAG_T, 0, st>>>(cell, off, px, py, pz, n, Nx, out);
+}
 
 void launch_snapshot(DevSpecies sp, int64_t n, const SnapParams& S, float* d_out, float* chi_out,
                      unsigned long long* out, cudaStream_t st) {

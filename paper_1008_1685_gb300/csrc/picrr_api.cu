@@ -614,16 +614,44 @@ pic_status run_load_particles_f32(Batch* b, int id, int species, int64_t n, cons
     pic_status st = check_species_args(b, r, species, n, weight, charge, mass);
     if (st != PIC_OK) return st;
     if (n > 0 && (!cell || !off || !px || !py || !pz)) return fail(b, PIC_ERR_INVALID_ARG, "NULL array");
-    bool sorted = true;
-    for (int64_t i = 0; i < n; ++i) {
-        if (cell[i] < 0 || cell[i] >= r.Nx) return fail(b, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
-        if (!(off[i] >= 0.0f && off[i] < 1.0f)) return fail(b, PIC_ERR_INVALID_ARG, "offset out of [0, 1)");
-        if (!std::isfinite(px[i]) || !std::isfinite(py[i]) || !std::isfinite(pz[i]))
-            return fail(b, PIC_ERR_INVALID_ARG, "non-finite momentum");
-        if (i > 0 && cell[i] < cell[i - 1]) sorted = false;
+    // upload as given, then check on the device: ranges, finiteness and cell order
+    st = run_upload(b, r, species, n, cell, off, px, py, pz, nullptr, weight, charge, mass);
+    if (st != PIC_OK || n == 0) return st;
+    unsigned long long chk[3] = {0, 0, 0};
+    {
+        const DevSpecies& d = r.dev.sp[species][b->cur];
+        PIC_CK(b, cudaMemsetAsync(b->snap_out, 0, 4 * sizeof(unsigned long long), b->stream));
+        launch_validate(d.cell, d.off, d.px, d.py, d.pz, n, r.Nx, b->snap_out, b->stream);
+        b->launches++;
+        PIC_CK(b, cudaMemcpyAsync(chk, b->snap_out, sizeof(chk), cudaMemcpyDeviceToHost, b->stream));
+        PIC_CK(b, cudaStreamSynchronize(b->stream));
     }
-    if (sorted) return run_upload(b, r, species, n, cell, off, px, py, pz, nullptr, weight, charge, mass);
-    // units need cell order: stable sort; ids keep the load order
+    if (chk[0] == 0 && chk[1] == 0 && chk[2] == 0) return PIC_OK;
+    // not usable as uploaded: release it (the species stays unloaded)
+    {
+        std::vector<std::pair<void*, size_t>> keep;
+        for (auto& a : r.mem) {
+            bool mine = false;
+            for (int x = 0; x < 2; ++x) {
+                const DevSpecies& d = r.dev.sp[species][x];
+                for (const void* q : {static_cast<const void*>(d.cell), static_cast<const void*>(d.off),
+                                      static_cast<const void*>(d.px), static_cast<const void*>(d.py),
+                                      static_cast<const void*>(d.pz), static_cast<const void*>(d.id)})
+                    mine = mine || a.first == q;
+            }
+            if (mine) {
+                cudaFreeAsync(a.first, b->stream);
+                b->bytes -= a.second;
+            } else {
+                keep.push_back(a);
+            }
+        }
+        r.mem.swap(keep);
+        clear_species(r, species);
+    }
+    if (chk[0]) return fail(b, PIC_ERR_INVALID_ARG, "cell out of [0, Nx)");
+    if (chk[1]) return fail(b, PIC_ERR_INVALID_ARG, "offset out of [0, 1) or non-finite momentum");
+    // units need cell order: stable sort on the host; ids keep the load order
     std::vector<int64_t> order(static_cast<size_t>(n));
     for (int64_t i = 0; i < n; ++i) order[static_cast<size_t>(i)] = i;
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) { return cell[a] < cell[c]; });
@@ -1667,6 +1695,33 @@ pic_status pic_set_timing(pic_sim* s, int on) {
 
 const char* pic_last_error(const pic_sim* s) { return s ? s->b->err.c_str() : g_null_error.c_str(); }
 
+pic_status pic_selftest_wait_timeout(int device, double* seconds) {
+    if (seconds) *seconds = 0.0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "bad device");
+    }
+    int* d_status = nullptr;
+    int h = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaMalloc(&d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        launch_wait_selftest(d_status, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d_status) cudaFree(d_status);
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "wait self-test");
+    if (h & ST_TIMEOUT) return fail(nullptr, PIC_ERR_TIMEOUT, "bounded device wait gave up (expected)");
+    return PIC_OK;
+}
+
 pic_status pic_destroy(pic_sim* s) {
     if (!s) return PIC_OK;
     batch_destroy(s->b);
@@ -1795,6 +1850,19 @@ pic_status pic_batch_read_fields(pic_batch* h, int run, int comp, int64_t cap, d
     if (st != PIC_OK) return st;
     DeviceGuard g(h->b->device);
     return run_read_fields(h->b, run, comp, cap, out, n);
+}
+
+pic_status pic_batch_stop_run(pic_batch* h, int run) {
+    pic_status st = check_run(h, run);
+    if (st != PIC_OK) return st;
+    Batch* b = h->b;
+    RunHost& r = b->runs[run];
+    if (!r.active) return PIC_OK;  // not stepping (pending, finished or stopped)
+    DeviceGuard g(b->device);
+    if (b->since_sort > 0) rad_flush(b);  // the run takes its radiated energy with it
+    deactivate(b, run);
+    if ((st = upload_table(b)) != PIC_OK) return st;
+    return upload_blocks(b);
 }
 
 pic_status pic_batch_release_run(pic_batch* h, int run) {

@@ -154,6 +154,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bounded wait: returns false after WAIT_LIMIT polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     for (int it = 0; it < WAIT_LIMIT; ++it)
@@ -227,6 +231,9 @@ struct SnapParams {
     const float* F[5];
     float eps, ecr_inv, chi_flag;
 };
+void launch_wait_selftest(int* status, cudaStream_t st);
+void launch_validate(const int32_t* cell, const float* off, const float* px, const float* py, const float* pz,
+                     int64_t n, int Nx, unsigned long long* out, cudaStream_t st);
 void launch_electron_scan(const pic_electron_case* cases, int64_t n, int integrator, int flags, double dt,
                           int64_t nsteps, int every, double eps, double* out, int64_t nsamples, cudaStream_t st);
 

@@ -41,6 +41,7 @@ struct Request {
     double work = 0.0;  // particles x steps
     Clock::time_point submitted;
     ReqState state = QUEUED;
+    bool cancel = false;  // asked to stop while running
     int run = -1;
     int64_t steps_seen = 0;
     std::vector<double> ion, el;
@@ -221,6 +222,31 @@ void pic_server::run() {
         }
         for (Request* r : ended) finish_run(r);
         running.swap(still);
+        // cancelled requests leave the batch between chunks
+        std::vector<Request*> keep;
+        for (Request* r : running) {
+            bool c;
+            {
+                std::lock_guard<std::mutex> lk(m);
+                c = r->cancel;
+            }
+            if (!c) {
+                keep.push_back(r);
+                continue;
+            }
+            pic_batch_stop_run(batch, r->run);
+            pic_batch_release_run(batch, r->run);
+            std::lock_guard<std::mutex> lk(m);
+            r->run = -1;
+            resident -= r->particles;
+            st.running--;
+            r->state = FAILED;
+            r->status = PIC_ERR_STATE;
+            r->err = "cancelled";
+            st.failed++;
+            cv_done.notify_all();
+        }
+        running.swap(keep);
     }
 }
 
@@ -319,6 +345,33 @@ pic_status pic_server_set_policy(pic_server* v, int policy, int64_t max_resident
     v->max_resident = max_resident_particles;
     v->cv_work.notify_one();
     return PIC_OK;
+}
+
+pic_status pic_server_cancel(pic_server* v, int64_t ticket) {
+    if (!v) return sfail(PIC_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(v->m);
+    auto it = v->reqs.find(ticket);
+    if (it == v->reqs.end()) return sfail(PIC_ERR_INVALID_ARG, "unknown ticket");
+    Request* r = it->second.get();
+    if (r->state == QUEUED) {
+        for (auto q = v->queue.begin(); q != v->queue.end(); ++q)
+            if (*q == ticket) {
+                v->queue.erase(q);
+                break;
+            }
+        v->st.queued = static_cast<int64_t>(v->queue.size());
+        r->state = FAILED;
+        r->status = PIC_ERR_STATE;
+        r->err = "cancelled";
+        v->st.failed++;
+        v->cv_done.notify_all();
+        return PIC_OK;
+    }
+    if (r->state == RUNNING) {
+        r->cancel = true;
+        return PIC_OK;
+    }
+    return sfail(PIC_ERR_STATE, "request already finished");
 }
 
 pic_status pic_server_stats(pic_server* v, pic_server_stats_t* out) {

@@ -234,6 +234,37 @@ def test_state_errors_and_budget(picrr):
     small.step(1)
 
 
+def test_particle_upload_is_checked_on_the_device(picrr):
+    """Uploaded particles are checked on the GPU: a cell outside the grid, an
+    offset outside [0, 1) or a non-finite momentum is rejected and leaves the
+    species unloaded; particles not in cell order are put in order (their
+    read-out keeps the load order)."""
+    g = picrr.Sim(length_lambda=2, cells_per_lambda=50)
+    nx = g.nx
+    n = 1001
+    rng = np.random.default_rng(3)
+    cell = np.sort(rng.integers(0, nx, n)).astype(np.int32)
+    off = rng.random(n).astype(np.float32)
+    p = rng.normal(size=(3, n)).astype(np.float32)
+    bad = [("cell", cell.copy()), ("off", off.copy()), ("px", p[0].copy())]
+    bad[0][1][500] = nx
+    bad[1][1][7] = 1.0
+    bad[2][1][1000] = np.inf
+    for what, arr in bad:
+        args = dict(cell=cell, off=off, px=p[0])
+        args[what] = arr
+        with pytest.raises(picrr.PicError) as e:
+            g.load_particles_f32(0, args["cell"], args["off"], args["px"], p[1], p[2], 0.01, -1.0, 1.0)
+        assert e.value.status == -1, what
+    perm = rng.permutation(n)  # out of cell order: sorted on the way in
+    g.load_particles_f32(0, cell[perm], off[perm], p[0][perm], p[1][perm], p[2][perm], 0.01, -1.0, 1.0)
+    got = g.particles(0)
+    np.testing.assert_array_equal(got["px"], p[0][perm])
+    np.testing.assert_allclose(got["x"], (cell[perm] + off[perm].astype(np.float64)) * g.dx, rtol=1e-6)
+    g.step(3)
+    g.close()
+
+
 def test_empty_and_single_species(picrr):
     g, o = pair(picrr, length_lambda=2, cells_per_lambda=50)
     cell, off, px, py, pz = synth.random_particles(5, 10, 90, pscale=3.0, seed=2)

@@ -143,3 +143,39 @@ def test_admission_order_policy(picrr, policy):
     for res, d in ((rb, big), (rm, medium), (rs, small)):
         assert_same(res, solo(picrr, d), d["seed"])
     srv.close()
+
+
+def test_cancel_queued_and_running(picrr):
+    """A cancelled queued request is dropped; a cancelled running one leaves the
+    batch at the end of the step chunk and frees its memory; the others are
+    unaffected (their results equal their solo runs)."""
+    long_run = dict(RUNS[1], seed=41, steps=4000)
+    other = dict(RUNS[0], seed=42)
+    queued = dict(RUNS[2], seed=43)
+    srv = picrr.Server(CPL, max_runs=2, chunk_steps=32)
+    kw = dict(nbins=NB, ion_e_max=ION_MAX, el_e_max=EL_MAX)
+    # only one run at a time: the queued request waits behind the first
+    srv.set_policy(picrr.SERVE_FIFO, 2 * long_run["ppc"] * round(long_run["foil_thickness"] * CPL))
+    ta = srv.submit(**kw, **desc(long_run))
+    tq = srv.submit(**kw, **desc(queued))
+    tb = srv.submit(**kw, **desc(other))
+    srv.cancel(tq)
+    with pytest.raises(picrr.PicError) as e:
+        srv.result(tq, wait_s=10.0)
+    assert e.value.status == -2 and "cancelled" in str(e.value)
+    t0 = time.time()
+    while srv.stats()["batch_steps"] < 200 and time.time() - t0 < 60:
+        time.sleep(0.001)
+    srv.cancel(ta)
+    with pytest.raises(picrr.PicError) as e:
+        srv.result(ta, wait_s=60.0)
+    assert e.value.status == -2
+    rb = srv.result(tb, wait_s=300.0)
+    st = srv.stats()
+    assert st["completed"] == 1 and st["failed"] == 2 and st["running"] == 0
+    assert st["batch_steps"] < long_run["steps"]  # the long run did not run to its end
+    assert_same(rb, solo(picrr, other), other["seed"])
+    with pytest.raises(picrr.PicError) as e:
+        srv.cancel(tb)
+    assert e.value.status == -1  # already fetched: unknown ticket
+    srv.close()
