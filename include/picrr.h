@@ -233,6 +233,19 @@ const char* pic_last_error(const pic_sim* sim);
 /* Free everything; NULL is accepted. */
 pic_status pic_destroy(pic_sim* sim);
 
+/* Checkpoint: write the run's complete state (fields of the current step,
+ * the last step's current, particles in cell order with their ids, species
+ * constants, laser, energy tallies, step count) to a binary file at path.  If
+ * particles moved since the last sort, the run is sorted first (that changes
+ * only the order of single-precision sums of later steps).  pic_restore
+ * creates a new handle on `device` in that state (sort_interval as in
+ * pic_config, 0 selects 8); stepping it continues the run: saved on a sort
+ * step, the continuation is bit-identical to the uninterrupted run. */
+pic_status pic_save(pic_sim* sim, const char* path);
+/* The configuration of a handle (as created or restored; sort_interval current). */
+pic_status pic_get_config(const pic_sim* sim, pic_config* out);
+pic_status pic_restore(const char* path, int device, int sort_interval, pic_sim** out);
+
 /* Self-test of failure detection on the device: launches one small kernel
  * whose mbarrier wait can never complete (it expects two arrivals and gets
  * one).  The wait is the bounded one every kernel of this library uses; it

@@ -35,7 +35,8 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_server_last_error", "pic_server_destroy", "pic_tune_shapes",
            "pic_batch_tune_shapes", "pic_set_shapes", "pic_batch_set_shapes", "pic_server_set_policy",
            "pic_snapshot", "pic_batch_snapshot",
-           "pic_electron_scan", "pic_selftest_wait_timeout", "pic_batch_stop_run", "pic_server_cancel")
+           "pic_electron_scan", "pic_selftest_wait_timeout", "pic_batch_stop_run", "pic_server_cancel",
+           "pic_save", "pic_restore", "pic_get_config")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -192,6 +193,9 @@ def library():
                                         C.c_double, C.c_int, dp, i64]
         L.pic_selftest_wait_timeout.argtypes = [C.c_int, dp]
         L.pic_batch_stop_run.argtypes = [vp, C.c_int]
+        L.pic_save.argtypes = [vp, C.c_char_p]
+        L.pic_restore.argtypes = [C.c_char_p, C.c_int, C.c_int, C.POINTER(vp)]
+        L.pic_get_config.argtypes = [vp, C.POINTER(Config)]
         L.pic_server_cancel.argtypes = [vp, i64]
         L.pic_snapshot.argtypes = [vp, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp, C.POINTER(i64)]
         L.pic_batch_snapshot.argtypes = [vp, C.c_int, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp,
@@ -270,19 +274,37 @@ class Sim:
     """One simulation handle (pic_create ... pic_destroy)."""
 
     def __init__(self, length_lambda, cells_per_lambda, cfl=0.95, lambda_um=0.8, rr_on=True,
-                 sort_interval=8, seed=1, device=0, source_node=8, hbm_budget_bytes=0):
+                 sort_interval=8, seed=1, device=0, source_node=8, hbm_budget_bytes=0, _handle=None):
         self._L = library()
-        cfg = Config(length_lambda, cells_per_lambda, cfl, lambda_um, int(rr_on), sort_interval, seed,
-                     device, source_node, hbm_budget_bytes)
-        h = C.c_void_p()
-        rc = self._L.pic_create(C.byref(cfg), C.byref(h))
-        if rc != 0:
-            raise PicError(rc, self._L.pic_last_error(None).decode())
+        if _handle is None:
+            cfg = Config(length_lambda, cells_per_lambda, cfl, lambda_um, int(rr_on), sort_interval, seed,
+                         device, source_node, hbm_budget_bytes)
+            h = C.c_void_p()
+            rc = self._L.pic_create(C.byref(cfg), C.byref(h))
+            if rc != 0:
+                raise PicError(rc, self._L.pic_last_error(None).decode())
+        else:
+            h = _handle
         self._h = h
         self.cells_per_lambda = cells_per_lambda
         self.nx = int(round(length_lambda * cells_per_lambda))
         self.dx = 2 * np.pi / cells_per_lambda
         self.dt = cfl * self.dx
+
+    @classmethod
+    def restore(cls, path, device=0, sort_interval=0):
+        """A new handle in the state saved by save() (pic_restore)."""
+        L = library()
+        h = C.c_void_p()
+        rc = L.pic_restore(os.fsencode(path), device, sort_interval, C.byref(h))
+        if rc != 0:
+            raise PicError(rc, L.pic_last_error(None).decode())
+        cfg = Config()
+        L.pic_get_config(h, C.byref(cfg))
+        return cls(cfg.length_lambda, cfg.cells_per_lambda, cfg.cfl, _handle=h)
+
+    def save(self, path):
+        self._check(self._L.pic_save(self._h, os.fsencode(path)))
 
     def _check(self, rc):
         if rc != 0:

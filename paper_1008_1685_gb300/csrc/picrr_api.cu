@@ -104,6 +104,7 @@ struct RunHost {
     LaserParams laser{};
     bool laser_set = false, fields_set = false;
     int64_t admit_step = 0;    // batch step of its first step
+    int64_t t_offset = 0;      // steps the run had made before it was restored from a checkpoint
     int64_t steps_target = 0;  // 0: unlimited
     int64_t steps_done = 0;
     int pbuf = 0, fbuf = 0;    // particle / field buffer of a finished run
@@ -963,7 +964,7 @@ pic_status upload_incident(Batch* b, int steps) {
         for (int i = 0; i < b->max_runs; ++i) {
             const RunHost& r = b->runs[i];
             if (!r.used || !r.active) continue;
-            const double tn = static_cast<double>(b->gstep + j - r.admit_step) * b->dt;
+            const double tn = static_cast<double>(b->gstep + j - r.admit_step + r.t_offset) * b->dt;
             const double ts[3] = {tn, tn + 0.5 * b->dt + 0.5 * b->dx, tn + b->dt};
             for (int k = 0; k < 3; ++k) incident(r.laser, ts[k], &hj[6 * i + 2 * k], &hj[6 * i + 2 * k + 1]);
         }
@@ -1473,6 +1474,128 @@ pic_status run_read_fields(Batch* b, int id, int comp, int64_t cap, double* out,
     return PIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoint and restore of one run
+// ---------------------------------------------------------------------------
+constexpr char kMagic[8] = {'P', 'I', 'C', 'R', 'R', 'C', 'K', '1'};
+
+struct CkHeader {
+    char magic[8];
+    int32_t version, nx, source_node, rr;
+    double length_lambda, cells_per_lambda, cfl, lambda_um;
+    uint64_t seed;
+    int64_t steps;            // steps the run has made
+    int32_t laser_on, pol, env, loaded[2];
+    double a0, tau, rise;
+    int64_t n[2];
+    double w[2], q[2], m[2];
+    double tally[4];
+    int64_t glen;
+};
+
+pic_status run_save(Batch* b, int id, const char* path) {
+    RunHost& r = b->runs[id];
+    if (r.active && b->since_sort > 0) do_sort(b);  // saved in cell order (the sort also flushes the radiated partials)
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(b, PIC_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+    CkHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.nx = r.Nx;
+    h.source_node = r.is;
+    h.rr = r.rr;
+    h.length_lambda = r.length_lambda;
+    h.cells_per_lambda = b->cfg.cells_per_lambda;
+    h.cfl = b->cfl;
+    h.lambda_um = b->cfg.lambda_um;
+    h.seed = r.seed;
+    h.steps = r.steps_done + r.t_offset;
+    h.laser_on = r.laser_set ? 1 : 0;
+    h.pol = r.laser.pol;
+    h.env = r.laser.env;
+    h.a0 = r.laser.a0;
+    h.tau = r.laser.tau;
+    h.rise = r.laser.rise;
+    for (int s = 0; s < 2; ++s) {
+        h.loaded[s] = r.sp[s].loaded ? 1 : 0;
+        h.n[s] = r.sp[s].loaded ? r.sp[s].n : 0;
+        h.w[s] = r.sp[s].w;
+        h.q[s] = r.sp[s].q;
+        h.m[s] = r.sp[s].m;
+    }
+    h.glen = static_cast<int64_t>(r.glen);
+    cudaError_t e = cudaMemcpyAsync(h.tally, r.dev.tally, sizeof(h.tally), cudaMemcpyDeviceToHost, b->stream);
+    std::vector<char> buf;
+    auto put = [&](const void* dev, size_t bytes) {
+        buf.resize(bytes);
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(buf.data(), dev, bytes, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        return e == cudaSuccess && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    };
+    bool ok = (e = cudaStreamSynchronize(b->stream)) == cudaSuccess && std::fwrite(&h, sizeof(h), 1, f) == 1;
+    const int fb = run_fbuf(b, r), pb = run_pbuf(b, r);
+    for (int c = 0; c < 5 && ok; ++c) ok = put(r.dev.F[fb][c], r.glen * 4);
+    for (int c = 0; c < 3 && ok; ++c) ok = put(r.dev.Jf[c], r.glen * 4);
+    for (int s = 0; s < 2 && ok; ++s) {
+        if (!h.loaded[s] || h.n[s] == 0) continue;
+        const DevSpecies& d = r.dev.sp[s][pb];
+        const size_t by = static_cast<size_t>(h.n[s]) * 4;
+        for (const void* a : {static_cast<const void*>(d.cell), static_cast<const void*>(d.off),
+                              static_cast<const void*>(d.px), static_cast<const void*>(d.py),
+                              static_cast<const void*>(d.pz), static_cast<const void*>(d.id)})
+            ok = ok && put(a, by);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (e != cudaSuccess) return cuda_fail(b, e, "save");
+    if (!ok) return fail(b, PIC_ERR_INVALID_ARG, std::string("write failed: ") + path);
+    return PIC_OK;
+}
+
+// Restore into a freshly opened run slot (grid allocated, nothing loaded).
+pic_status run_restore(Batch* b, int id, FILE* f, const CkHeader& h) {
+    RunHost& r = b->runs[id];
+    std::vector<char> buf;
+    auto get = [&](void* dev, size_t bytes) -> pic_status {
+        buf.resize(bytes);
+        if (bytes && std::fread(buf.data(), 1, bytes, f) != bytes)
+            return fail(b, PIC_ERR_INVALID_ARG, "checkpoint file is truncated");
+        cudaError_t e = bytes ? cudaMemcpyAsync(dev, buf.data(), bytes, cudaMemcpyHostToDevice, b->stream)
+                              : cudaSuccess;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        return e == cudaSuccess ? PIC_OK : cuda_fail(b, e, "restore");
+    };
+    pic_status st = PIC_OK;
+    for (int c = 0; c < 5 && st == PIC_OK; ++c) st = get(r.dev.F[0][c], r.glen * 4);
+    for (int c = 0; c < 3 && st == PIC_OK; ++c) st = get(r.dev.Jf[c], r.glen * 4);
+    for (int s = 0; s < 2 && st == PIC_OK; ++s) {
+        if (!h.loaded[s]) continue;
+        if ((st = alloc_species(b, r, s, h.n[s])) != PIC_OK) break;
+        const DevSpecies& d = r.dev.sp[s][b->cur];
+        const size_t by = static_cast<size_t>(h.n[s]) * 4;
+        for (void* a : {static_cast<void*>(d.cell), static_cast<void*>(d.off), static_cast<void*>(d.px),
+                        static_cast<void*>(d.py), static_cast<void*>(d.pz), static_cast<void*>(d.id)})
+            if (st == PIC_OK) st = get(a, by);
+        r.sp[s].loaded = true;
+        r.sp[s].w = h.w[s];
+        r.sp[s].q = h.q[s];
+        r.sp[s].m = h.m[s];
+    }
+    if (st != PIC_OK) return st;
+    PIC_CK(b, cudaMemcpy(r.dev.tally, h.tally, sizeof(h.tally), cudaMemcpyHostToDevice));
+    if (h.laser_on) {
+        r.laser.on = 1;
+        r.laser.pol = h.pol;
+        r.laser.env = h.env;
+        r.laser.a0 = h.a0;
+        r.laser.tau = h.tau;
+        r.laser.rise = h.rise;
+        r.laser_set = true;
+    }
+    r.fields_set = true;
+    r.t_offset = h.steps;
+    return PIC_OK;
+}
+
 void fill_stats(Batch* b, pic_stats_t* out) {
     std::memset(out, 0, sizeof(*out));
     out->steps = b->gstep;
@@ -1694,6 +1817,73 @@ pic_status pic_set_timing(pic_sim* s, int on) {
 }
 
 const char* pic_last_error(const pic_sim* s) { return s ? s->b->err.c_str() : g_null_error.c_str(); }
+
+pic_status pic_get_config(const pic_sim* s, pic_config* out) {
+    if (!s || !out) return PIC_ERR_INVALID_ARG;
+    const Batch* b = s->b;
+    const RunHost& r = b->runs[0];
+    *out = b->cfg;
+    out->length_lambda = r.length_lambda;
+    out->rr_on = r.rr;
+    out->seed = r.seed;
+    out->source_node = r.is;
+    out->sort_interval = b->sort_interval;
+    return PIC_OK;
+}
+
+pic_status pic_save(pic_sim* s, const char* path) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    if (!path) return fail(s->b, PIC_ERR_INVALID_ARG, "path is NULL");
+    DeviceGuard g(s->b->device);
+    return run_save(s->b, 0, path);
+}
+
+pic_status pic_restore(const char* path, int device, int sort_interval, pic_sim** out) {
+    if (!out) return fail(nullptr, PIC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(nullptr, PIC_ERR_INVALID_ARG, "path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(nullptr, PIC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    CkHeader h{};
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 ||
+        h.n[0] < 0 || h.n[1] < 0 || h.n[0] > 2147483647LL - 64 || h.n[1] > 2147483647LL - 64) {
+        std::fclose(f);
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "not a picrr checkpoint (or another version)");
+    }
+    pic_config cfg{};
+    cfg.length_lambda = h.length_lambda;
+    cfg.cells_per_lambda = h.cells_per_lambda;
+    cfg.cfl = h.cfl;
+    cfg.lambda_um = h.lambda_um;
+    cfg.rr_on = h.rr;
+    cfg.sort_interval = sort_interval;
+    cfg.seed = h.seed;
+    cfg.device = device;
+    cfg.source_node = h.source_node;
+    pic_sim* s = nullptr;
+    pic_status st = pic_create(&cfg, &s);
+    if (st != PIC_OK) {
+        std::fclose(f);
+        return st;
+    }
+    if (s->b->runs[0].Nx != h.nx || static_cast<int64_t>(s->b->runs[0].glen) != h.glen) {
+        std::fclose(f);
+        pic_destroy(s);
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "checkpoint grid does not match its configuration");
+    }
+    {
+        DeviceGuard g(s->b->device);
+        st = run_restore(s->b, 0, f, h);
+    }
+    std::fclose(f);
+    if (st != PIC_OK) {
+        g_null_error = s->b->err;
+        pic_destroy(s);
+        return st;
+    }
+    *out = s;
+    return PIC_OK;
+}
 
 pic_status pic_selftest_wait_timeout(int device, double* seconds) {
     if (seconds) *seconds = 0.0;
