@@ -43,7 +43,7 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # DRAM traffic of one push launch of this workload, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles,
 # 16384 particles per unit, sort every 32 steps); reported when the run matches
-PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=32,
+PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=32, particles_per_thread=4,
                     bytes=1_280_281_856 + 1_219_174_912)
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
@@ -383,7 +383,7 @@ def e2e_run(picrr, torch, device, steps, host, shapes=None):
         s.load_particles_f32(sp, c, o, x, y, z, *host["species"][sp])
     s.inject_laser(w["a0"], w["pol"], 0, w["duration"])
     if shapes:
-        s.set_shapes(shapes["unit_particles"], shapes["sort_interval"])
+        s.set_shapes(shapes["unit_particles"], shapes["sort_interval"], shapes["particles_per_thread"])
     s.step(steps)
     counts, rad = s.spectra(1, 200, 0.0, 2000.0)
     en = s.energy()
@@ -406,7 +406,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no tuner run)")
     ap.add_argument("--shapes", default=None,
-                    help="UNIT,INTERVAL: set these launch shapes instead of running the tuner (profiling)")
+                    help="UNIT,INTERVAL[,PARTICLES_PER_THREAD]: set these launch shapes instead of running the "
+                         "tuner (profiling)")
     ap.add_argument("--scan-runs", type=int, default=SCAN["n_runs"], help="runs of the batched scan (0: skip)")
     ap.add_argument("--scan-steps", type=int, default=0, help="cut the scan runs to this many steps (profiling)")
     ap.add_argument("--plain-runs", type=int, default=8,
@@ -447,24 +448,26 @@ def main():
     w = dict(LARGE, ppc=args.ppc)
     shapes = None
     if args.shapes:
-        u, k = (int(v) for v in args.shapes.split(","))
-        shapes = {"unit_particles": u, "sort_interval": k, "tuned": False}
+        v = [int(x) for x in args.shapes.split(",")]
+        shapes = {"unit_particles": v[0], "sort_interval": v[1], "particles_per_thread": v[2] if len(v) > 2 else 4,
+                  "tuned": False}
     elif not args.no_tune:
         # launch shapes picked by the tuner on an identical run (its trial steps are
         # real steps, so the measured run starts fresh)
         t = make_sim(picrr, local)
         t.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
         t.inject_laser(w["a0"], w["pol"], 0, w["duration"])
-        unit, interval, tms = t.tune_shapes(64)
+        unit, interval, ppt, tms = t.tune_shapes(64)
         t.close()
-        shapes = {"unit_particles": unit, "sort_interval": interval, "tuned": True,
-                  "trial_ms_per_step": {"unit_2048_4096_8192_16384": [round(v, 4) for v in tms[:4]],
-                                        "interval_4_8_16_32": [round(v, 4) for v in tms[4:]]}}
+        shapes = {"unit_particles": unit, "sort_interval": interval, "particles_per_thread": ppt, "tuned": True,
+                  "trial_ms_per_step": {"particles_per_thread_4_2": [round(v, 4) for v in tms[:2]],
+                                        "unit_2048_4096_8192_16384": [round(v, 4) for v in tms[2:6]],
+                                        "interval_4_8_16_32": [round(v, 4) for v in tms[6:]]}}
     sim = make_sim(picrr, local)
     sim.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
     sim.inject_laser(w["a0"], w["pol"], 0, w["duration"])
     if shapes:
-        sim.set_shapes(shapes["unit_particles"], shapes["sort_interval"])
+        sim.set_shapes(shapes["unit_particles"], shapes["sort_interval"], shapes["particles_per_thread"])
     stream = torch.cuda.current_stream()
     sim.set_stream(stream.cuda_stream)
     sim.step(args.warmup)
@@ -497,7 +500,8 @@ def main():
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     traffic = None
     if (shapes and n_active == PUSH_TRAFFIC["particles"] and shapes["unit_particles"] == PUSH_TRAFFIC["unit_particles"]
-            and shapes["sort_interval"] == PUSH_TRAFFIC["sort_interval"]):
+            and shapes["sort_interval"] == PUSH_TRAFFIC["sort_interval"]
+            and shapes["particles_per_thread"] == PUSH_TRAFFIC["particles_per_thread"]):
         traffic = PUSH_TRAFFIC["bytes"]
     sim.close()
 

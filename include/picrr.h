@@ -199,24 +199,30 @@ typedef struct {
 
 /* Launch shapes.  unit_particles: the most particles one CTA of the fused
  * push kernel takes (its work unit), a power of two in [1024, 16384]
- * (default 4096); sort_interval in [1, 32].  Larger units amortise each
- * CTA's fixed costs on dense foils; smaller ones keep the GPU busy when few
- * particles are spread thinly.  A new unit size takes effect at once (the
- * run is sorted if needed and its unit table rebuilt).  Both change only the
- * order of single-precision sums. */
-pic_status pic_set_shapes(pic_sim* sim, int unit_particles, int sort_interval);
+ * (default 4096); sort_interval in [1, 32]; particles_per_thread: 4 or 2,
+ * the particles each thread of the push kernel takes per round (4: 128-bit
+ * loads and stores and the fewest instructions per particle, for dense foils;
+ * 2: fewer registers and more warps per SM, which hides the latency of
+ * deposits that scatter over many cells; default 2, so that a run gives the
+ * same bits alone and in a batch; the tuner picks 4 for dense foils).  Larger units amortise each CTA's fixed costs on dense foils;
+ * smaller ones keep the GPU busy when few particles are spread thinly.  A new
+ * unit size takes effect at once (the run is sorted if needed and its unit
+ * table rebuilt).  None of them changes more than the order of
+ * single-precision sums. */
+pic_status pic_set_shapes(pic_sim* sim, int unit_particles, int sort_interval, int particles_per_thread);
 
 /* Shape tuner.  Steps the run for a trial of about steps_per_candidate steps
- * (rounded to whole sort intervals, after one warm-up interval) at each unit
- * size of {2048, 4096, 8192, 16384} with the current sort interval, keeps
- * the fastest, then at each sort interval of {4, 8, 16, 32}; measures the wall
- * time per step (CUDA graphs, as pic_step_n runs them) and keeps the fastest
- * pair.  *unit_particles and *sort_interval (nullable) receive it;
- * ms_per_step[8] (nullable) the measured times per step (unit sizes, then
+ * (rounded to whole sort intervals, after one warm-up interval) with 4 and 2
+ * particles per thread, keeps the faster, then at each unit size of {2048,
+ * 4096, 8192, 16384}, keeps the fastest, then at each sort interval of {4, 8,
+ * 16, 32}; measures the wall time per step (CUDA graphs, as pic_step_n runs
+ * them) and keeps the fastest shapes.  *unit_particles, *sort_interval and
+ * *particles_per_thread (nullable) receive them; ms_per_step[10] (nullable)
+ * the measured times per step (particles per thread 4, 2; unit sizes;
  * intervals; -1 where not measured).  The trial steps are real steps of the
  * run.  Timing must be off. */
 pic_status pic_tune_shapes(pic_sim* sim, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
-                           double* ms_per_step);
+                           int* particles_per_thread, double* ms_per_step);
 
 /* Counters and, when timing is on, CUDA-event times of each kernel class,
  * recorded on the launching stream.  With timing off, every whole sort
@@ -320,9 +326,9 @@ pic_status pic_batch_release_run(pic_batch* batch, int run);
  * called from any thread; its error message is pic_batch_last_error(NULL). */
 pic_status pic_batch_run_footprint(const pic_batch* batch, const pic_run_desc* desc, size_t* bytes);
 /* As pic_set_shapes / pic_tune_shapes, for all active runs of the batch together. */
-pic_status pic_batch_set_shapes(pic_batch* batch, int unit_particles, int sort_interval);
+pic_status pic_batch_set_shapes(pic_batch* batch, int unit_particles, int sort_interval, int particles_per_thread);
 pic_status pic_batch_tune_shapes(pic_batch* batch, int64_t steps_per_candidate, int* unit_particles,
-                                 int* sort_interval, double* ms_per_step);
+                                 int* sort_interval, int* particles_per_thread, double* ms_per_step);
 pic_status pic_batch_stats(pic_batch* batch, pic_stats_t* out);
 pic_status pic_batch_set_timing(pic_batch* batch, int on);
 const char* pic_batch_last_error(const pic_batch* batch);

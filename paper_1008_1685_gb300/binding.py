@@ -184,10 +184,11 @@ def library():
         L.pic_server_last_error.argtypes = [vp]
         L.pic_server_last_error.restype = C.c_char_p
         L.pic_server_destroy.argtypes = [vp]
-        L.pic_tune_shapes.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
-        L.pic_batch_tune_shapes.argtypes = [vp, i64, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
-        L.pic_set_shapes.argtypes = [vp, C.c_int, C.c_int]
-        L.pic_batch_set_shapes.argtypes = [vp, C.c_int, C.c_int]
+        ip = C.POINTER(C.c_int)
+        L.pic_tune_shapes.argtypes = [vp, i64, ip, ip, ip, dp]
+        L.pic_batch_tune_shapes.argtypes = [vp, i64, ip, ip, ip, dp]
+        L.pic_set_shapes.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.pic_batch_set_shapes.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.pic_server_set_policy.argtypes = [vp, C.c_int, i64]
         L.pic_electron_scan.argtypes = [C.POINTER(ElectronCase), i64, C.c_int, C.c_int, C.c_double, i64, C.c_int,
                                         C.c_double, C.c_int, dp, i64]
@@ -404,15 +405,17 @@ class Sim:
         return st.as_dict()
 
     def tune_shapes(self, steps_per_candidate=64):
-        """Pick the fastest work-unit size and sort interval by timing real steps.
-        Returns (unit_particles, sort_interval, ms_per_step[8])."""
-        u, c = C.c_int(0), C.c_int(0)
-        ms = np.full(8, -1.0)
-        self._check(self._L.pic_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), _dp(ms)))
-        return u.value, c.value, ms
+        """Pick the fastest particles per thread, work-unit size and sort interval
+        by timing real steps.  Returns (unit_particles, sort_interval,
+        particles_per_thread, ms_per_step[10])."""
+        u, c, w = C.c_int(0), C.c_int(0), C.c_int(0)
+        ms = np.full(10, -1.0)
+        self._check(self._L.pic_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), C.byref(w),
+                                            _dp(ms)))
+        return u.value, c.value, w.value, ms
 
-    def set_shapes(self, unit_particles, sort_interval):
-        self._check(self._L.pic_set_shapes(self._h, unit_particles, sort_interval))
+    def set_shapes(self, unit_particles, sort_interval, particles_per_thread=2):
+        self._check(self._L.pic_set_shapes(self._h, unit_particles, sort_interval, particles_per_thread))
 
     def set_timing(self, on=True):
         self._check(self._L.pic_set_timing(self._h, int(on)))
@@ -534,13 +537,14 @@ class Batch:
         return st.as_dict()
 
     def tune_shapes(self, steps_per_candidate=64):
-        u, c = C.c_int(0), C.c_int(0)
-        ms = np.full(8, -1.0)
-        self._check(self._L.pic_batch_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), _dp(ms)))
-        return u.value, c.value, ms
+        u, c, w = C.c_int(0), C.c_int(0), C.c_int(0)
+        ms = np.full(10, -1.0)
+        self._check(self._L.pic_batch_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c),
+                                                  C.byref(w), _dp(ms)))
+        return u.value, c.value, w.value, ms
 
-    def set_shapes(self, unit_particles, sort_interval):
-        self._check(self._L.pic_batch_set_shapes(self._h, unit_particles, sort_interval))
+    def set_shapes(self, unit_particles, sort_interval, particles_per_thread=2):
+        self._check(self._L.pic_batch_set_shapes(self._h, unit_particles, sort_interval, particles_per_thread))
 
     def set_timing(self, on=True):
         self._check(self._L.pic_batch_set_timing(self._h, int(on)))

@@ -59,8 +59,41 @@ __device__ __forceinline__ int comp(const int4& a, int j) { return j == 0 ? a.x 
 __device__ __forceinline__ float comp(const float4& a, int j) {
     return j == 0 ? a.x : j == 1 ? a.y : j == 2 ? a.z : a.w;
 }
+__device__ __forceinline__ int comp(const int2& a, int j) { return j == 0 ? a.x : a.y; }
+__device__ __forceinline__ float comp(const float2& a, int j) { return j == 0 ? a.x : a.y; }
 
-__global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) {
+// A thread takes W consecutive particles per round (one W x 4-byte slot of each
+// array).  W = 4: 128-bit loads and stores, fewest instructions per particle,
+// for dense foils.  W = 2: 64-bit, fewer registers and so more warps per SM,
+// which hides the latency of deposits that scatter over many cells (thinly
+// spread particles).
+template <int W>
+struct Slot;
+template <>
+struct Slot<4> {
+    using I = int4;
+    using F = float4;
+    static constexpr int MIN_BLOCKS = 4;
+    static __device__ __forceinline__ I empty_i() { return make_int4(-1, -1, -1, -1); }
+    static __device__ __forceinline__ F zero_f() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ I pack(const int (&v)[4]) { return make_int4(v[0], v[1], v[2], v[3]); }
+    static __device__ __forceinline__ F pack(const float (&v)[4]) { return make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <>
+struct Slot<2> {
+    using I = int2;
+    using F = float2;
+    static constexpr int MIN_BLOCKS = 6;
+    static __device__ __forceinline__ I empty_i() { return make_int2(-1, -1); }
+    static __device__ __forceinline__ F zero_f() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ I pack(const int (&v)[2]) { return make_int2(v[0], v[1]); }
+    static __device__ __forceinline__ F pack(const float (&v)[2]) { return make_float2(v[0], v[1]); }
+};
+
+template <int W>
+__global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(const PushParams P) {
+    using I = typename Slot<W>::I;
+    using F = typename Slot<W>::F;
     __shared__ __align__(128) float sF[5][WMAX];
     __shared__ __align__(16) unsigned long long sJ[3][WMAX];  // Jx (half nodes), Jy, Jz (nodes) of the window
     __shared__ __align__(8) uint64_t bar;
@@ -93,11 +126,11 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
     }
     __syncthreads();
     const DevSpecies sp = R.sp[s][P.cur];
-    // the unit's particles are read in 16-byte slots of 4, from the aligned slot
-    // before `start` to the aligned slot after `end`; the at most 3 particles
-    // of each neighbouring unit in those slots are never written here
-    const int base = start & ~3;
-    const int np4 = ((end + 3) & ~3) - base;
+    // the unit's particles are read in slots of W, from the aligned slot before
+    // `start` to the aligned slot after `end`; the at most W - 1 particles of
+    // each neighbouring unit in those slots are never written here
+    const int base = start & ~(W - 1);
+    const int npw = ((end + W - 1) & ~(W - 1)) - base;
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
 #pragma unroll
@@ -112,7 +145,7 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
     const int Nx = R.Nx;
     const float hq = 0.5f * qm * dt;
     const float jxf = qw / cfl;  // q w dx / dt
-    const int nslots = np4 >> 2;
+    const int nslots = npw / W;
     const int rounds = (nslots + PUSH_T - 1) / PUSH_T;
 
     const bool got = mbar_wait_bounded(&bar, 0);
@@ -130,22 +163,22 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
 
     for (int r = 0; r < rounds; ++r) {
         const int slot = r * PUSH_T + tid;
-        const int b4 = base + 4 * slot;
+        const int b4 = base + W * slot;
         const bool slot_ok = slot < nslots;
-        int4 c4 = make_int4(-1, -1, -1, -1);
-        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), x4 = o4, y4 = o4, z4 = o4;
+        I c4 = Slot<W>::empty_i();
+        F o4 = Slot<W>::zero_f(), x4 = o4, y4 = o4, z4 = o4;
         if (slot_ok) {
-            c4 = __ldcs(reinterpret_cast<const int4*>(sp.cell + b4));
-            o4 = __ldcs(reinterpret_cast<const float4*>(sp.off + b4));
-            x4 = __ldcs(reinterpret_cast<const float4*>(sp.px + b4));
-            y4 = __ldcs(reinterpret_cast<const float4*>(sp.py + b4));
-            z4 = __ldcs(reinterpret_cast<const float4*>(sp.pz + b4));
+            c4 = __ldcs(reinterpret_cast<const I*>(sp.cell + b4));
+            o4 = __ldcs(reinterpret_cast<const F*>(sp.off + b4));
+            x4 = __ldcs(reinterpret_cast<const F*>(sp.px + b4));
+            y4 = __ldcs(reinterpret_cast<const F*>(sp.py + b4));
+            z4 = __ldcs(reinterpret_cast<const F*>(sp.pz + b4));
         }
-        int cn[4];
-        float fo[4], qx[4], qy[4], qz[4];
-        bool act[4];
+        int cn[W];
+        float fo[W], qx[W], qy[W], qz[W];
+        bool act[W];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < W; ++j) {
             const int idx = b4 + j;
             int c = comp(c4, j);
             float f = comp(o4, j);
@@ -282,15 +315,15 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
 #pragma unroll
         for (int q = 0; q < 8; ++q) rv[q] = 0.f;
         if (slot_ok) {
-            if (b4 >= start && b4 + 3 < end) {
-                __stcs(reinterpret_cast<int4*>(sp.cell + b4), make_int4(cn[0], cn[1], cn[2], cn[3]));
-                __stcs(reinterpret_cast<float4*>(sp.off + b4), make_float4(fo[0], fo[1], fo[2], fo[3]));
-                __stcs(reinterpret_cast<float4*>(sp.px + b4), make_float4(qx[0], qx[1], qx[2], qx[3]));
-                __stcs(reinterpret_cast<float4*>(sp.py + b4), make_float4(qy[0], qy[1], qy[2], qy[3]));
-                __stcs(reinterpret_cast<float4*>(sp.pz + b4), make_float4(qz[0], qz[1], qz[2], qz[3]));
+            if (b4 >= start && b4 + W - 1 < end) {
+                __stcs(reinterpret_cast<I*>(sp.cell + b4), Slot<W>::pack(cn));
+                __stcs(reinterpret_cast<F*>(sp.off + b4), Slot<W>::pack(fo));
+                __stcs(reinterpret_cast<F*>(sp.px + b4), Slot<W>::pack(qx));
+                __stcs(reinterpret_cast<F*>(sp.py + b4), Slot<W>::pack(qy));
+                __stcs(reinterpret_cast<F*>(sp.pz + b4), Slot<W>::pack(qz));
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < W; ++j) {
                     if (!act[j]) continue;
                     sp.cell[b4 + j] = cn[j];
                     sp.off[b4 + j] = fo[j];
@@ -325,9 +358,12 @@ __global__ void __launch_bounds__(PUSH_T, 4) k_push_deposit(const PushParams P) 
 
 }  // namespace
 
-void launch_push(const PushParams& P, int grid, cudaStream_t st) {
+void launch_push(const PushParams& P, int grid, int slot_w, cudaStream_t st) {
     if (grid <= 0) return;
-    k_push_deposit<<<grid, PUSH_T, 0, st>>>(P);
+    if (slot_w == 2)
+        k_push_deposit<2><<<grid, PUSH_T, 0, st>>>(P);
+    else
+        k_push_deposit<4><<<grid, PUSH_T, 0, st>>>(P);
 }
 
 }  // namespace picrr

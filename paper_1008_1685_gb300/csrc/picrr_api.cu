@@ -118,6 +118,7 @@ struct Batch {
     pic_config cfg{};
     int device = 0, sort_interval = 8, max_runs = 1;
     int unit_p = UNIT_P;  // particles per work unit at most (a run-time shape)
+    int slot_w = 2;       // particles per thread and round of the push kernel (2 or 4; the tuner picks)
     double dx = 0, dt = 0, cfl = 0, eps = 0;
     cudaStream_t stream = nullptr, own_stream = nullptr;
     size_t bytes = 0, budget = 0;
@@ -1020,7 +1021,7 @@ pic_status chunk_graph(Batch* b, int par0, int cur, cudaGraphExec_t* out) {
     cudaStream_t cs = b->cap_stream;
     PIC_CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int j = 0; j < I; ++j) {
-        launch_push(push_params(b, par0 + j, j, cur), b->max_units, cs);
+        launch_push(push_params(b, par0 + j, j, cur), b->max_units, b->slot_w, cs);
         launch_field(field_params(b, par0 + j, j), b->nblk, cs);
     }
     launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, cs);
@@ -1093,7 +1094,7 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
         if ((st = upload_incident(b, 1)) != PIC_OK) return st;
         {
             Timed t(b, 0);
-            launch_push(push_params(b, b->gstep, b->since_sort, b->cur), b->max_units, b->stream);
+            launch_push(push_params(b, b->gstep, b->since_sort, b->cur), b->max_units, b->slot_w, b->stream);
         }
         {
             Timed t(b, 1);
@@ -1154,9 +1155,10 @@ int64_t units_needed(const Batch* b, int unit_p) {
 
 // Set the launch shapes: work-unit size (takes effect through a sort now, which
 // rebuilds the unit table) and sort interval.
-pic_status set_shapes(Batch* b, int unit_p, int interval) {
+pic_status set_shapes(Batch* b, int unit_p, int interval, int slot_w) {
     if (unit_p < UNIT_P_MIN || unit_p > UNIT_P_MAX || (unit_p & (unit_p - 1)) != 0)
         return fail(b, PIC_ERR_INVALID_ARG, "unit size must be a power of two in [1024, 16384]");
+    if (slot_w != 2 && slot_w != 4) return fail(b, PIC_ERR_INVALID_ARG, "particles per thread must be 2 or 4");
     if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 32]");
     pic_status st = activate_pending(b);
     if (st != PIC_OK) return st;
@@ -1179,7 +1181,8 @@ pic_status set_shapes(Batch* b, int unit_p, int interval) {
     }
     if (interval != b->sort_interval && b->since_sort > 0) do_sort(b);
     b->sort_interval = interval;
-    b->epoch++;
+    b->slot_w = slot_w;
+    b->epoch++;  // recapture the step graphs (interval, kernel variant)
     return PIC_OK;
 }
 
@@ -1189,19 +1192,21 @@ pic_status set_shapes(Batch* b, int unit_p, int interval) {
 // one warm-up interval and measures the wall time per step.  The trial steps
 // are real steps of every active run; the shapes change only the order of
 // single-precision sums.
-pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval_out, double* ms_out) {
+pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval_out, int* slot_out,
+                       double* ms_out) {
+    static const int slots[2] = {4, 2};
     static const int units[4] = {2048, 4096, 8192, 16384};
     static const int cand[4] = {4, 8, 16, 32};
     if (steps_per < 1) return fail(b, PIC_ERR_INVALID_ARG, "steps_per_candidate must be >= 1");
     if (b->timing) return fail(b, PIC_ERR_STATE, "turn timing off before tuning");
     if (ms_out)
-        for (int i = 0; i < 8; ++i) ms_out[i] = -1.0;
-    auto trial = [&](int unit_p, int interval, double* per) -> pic_status {
+        for (int i = 0; i < 10; ++i) ms_out[i] = -1.0;
+    auto trial = [&](int unit_p, int interval, int slot_w, double* per) -> pic_status {
         *per = -1.0;
         bool any = false;
         for (auto& r : b->runs) any = any || (r.used && r.active);
         if (!any) return PIC_OK;
-        pic_status st = set_shapes(b, unit_p, interval);
+        pic_status st = set_shapes(b, unit_p, interval, slot_w);
         if (st != PIC_OK) return st;
         int64_t done = 0;
         if ((st = batch_step(b, interval, &done)) != PIC_OK) return st;  // captures the shape's graphs
@@ -1215,12 +1220,22 @@ pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval
     };
     pic_status st = activate_pending(b);
     if (st != PIC_OK) return st;
-    int best_u = b->unit_p, best_i = b->sort_interval;
+    int best_w = b->slot_w, best_u = b->unit_p, best_i = b->sort_interval;
     double best = 1e300;
+    for (int c = 0; c < 2; ++c) {
+        double per;
+        if ((st = trial(best_u, best_i, slots[c], &per)) != PIC_OK) return st;
+        if (ms_out) ms_out[c] = per;
+        if (per > 0.0 && per < best) {
+            best = per;
+            best_w = slots[c];
+        }
+    }
+    best = 1e300;
     for (int c = 0; c < 4; ++c) {
         double per;
-        if ((st = trial(units[c], b->sort_interval, &per)) != PIC_OK) return st;
-        if (ms_out) ms_out[c] = per;
+        if ((st = trial(units[c], best_i, best_w, &per)) != PIC_OK) return st;
+        if (ms_out) ms_out[2 + c] = per;
         if (per > 0.0 && per < best) {
             best = per;
             best_u = units[c];
@@ -1229,17 +1244,18 @@ pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval
     best = 1e300;
     for (int c = 0; c < 4; ++c) {
         double per;
-        if ((st = trial(best_u, cand[c], &per)) != PIC_OK) return st;
-        if (ms_out) ms_out[4 + c] = per;
+        if ((st = trial(best_u, cand[c], best_w, &per)) != PIC_OK) return st;
+        if (ms_out) ms_out[6 + c] = per;
         if (per > 0.0 && per < best) {
             best = per;
             best_i = cand[c];
         }
     }
     if (best >= 1e300) return fail(b, PIC_ERR_STATE, "no active run stepped through a whole trial");
-    if ((st = set_shapes(b, best_u, best_i)) != PIC_OK) return st;
+    if ((st = set_shapes(b, best_u, best_i, best_w)) != PIC_OK) return st;
     if (unit_out) *unit_out = best_u;
     if (interval_out) *interval_out = best_i;
+    if (slot_out) *slot_out = best_w;
     return PIC_OK;
 }
 
@@ -1791,16 +1807,16 @@ pic_status pic_read_fields(pic_sim* s, int comp, int64_t cap, double* out, int64
 }
 
 pic_status pic_tune_shapes(pic_sim* s, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
-                           double* ms_per_step) {
+                           int* particles_per_thread, double* ms_per_step) {
     if (!s) return PIC_ERR_INVALID_ARG;
     DeviceGuard g(s->b->device);
-    return tune_shapes(s->b, steps_per_candidate, unit_particles, sort_interval, ms_per_step);
+    return tune_shapes(s->b, steps_per_candidate, unit_particles, sort_interval, particles_per_thread, ms_per_step);
 }
 
-pic_status pic_set_shapes(pic_sim* s, int unit_particles, int sort_interval) {
+pic_status pic_set_shapes(pic_sim* s, int unit_particles, int sort_interval, int particles_per_thread) {
     if (!s) return PIC_ERR_INVALID_ARG;
     DeviceGuard g(s->b->device);
-    return set_shapes(s->b, unit_particles, sort_interval);
+    return set_shapes(s->b, unit_particles, sort_interval, particles_per_thread);
 }
 
 pic_status pic_stats(pic_sim* s, pic_stats_t* out) {
@@ -2066,16 +2082,16 @@ pic_status pic_batch_release_run(pic_batch* h, int run) {
 }
 
 pic_status pic_batch_tune_shapes(pic_batch* h, int64_t steps_per_candidate, int* unit_particles, int* sort_interval,
-                                 double* ms_per_step) {
+                                 int* particles_per_thread, double* ms_per_step) {
     if (!h) return PIC_ERR_INVALID_ARG;
     DeviceGuard g(h->b->device);
-    return tune_shapes(h->b, steps_per_candidate, unit_particles, sort_interval, ms_per_step);
+    return tune_shapes(h->b, steps_per_candidate, unit_particles, sort_interval, particles_per_thread, ms_per_step);
 }
 
-pic_status pic_batch_set_shapes(pic_batch* h, int unit_particles, int sort_interval) {
+pic_status pic_batch_set_shapes(pic_batch* h, int unit_particles, int sort_interval, int particles_per_thread) {
     if (!h) return PIC_ERR_INVALID_ARG;
     DeviceGuard g(h->b->device);
-    return set_shapes(h->b, unit_particles, sort_interval);
+    return set_shapes(h->b, unit_particles, sort_interval, particles_per_thread);
 }
 
 pic_status pic_batch_stats(pic_batch* h, pic_stats_t* out) {

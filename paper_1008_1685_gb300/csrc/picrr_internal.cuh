@@ -178,7 +178,7 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (each defined in its own translation unit).
 // ---------------------------------------------------------------------------
-void launch_push(const PushParams& P, int grid, cudaStream_t st);
+void launch_push(const PushParams& P, int grid, int slot_w, cudaStream_t st);  // slot_w: 4 or 2 particles per thread and round
 void launch_field(const FieldParams& P, int grid, cudaStream_t st);
 
 struct SortParams {

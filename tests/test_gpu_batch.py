@@ -210,9 +210,9 @@ def test_graph_chunks_equal_single_launches(picrr):
 
 
 def test_shape_tuner(picrr):
-    """The tuner times real steps at unit sizes 2048..16384, then at sort
-    intervals 4..32, keeps the fastest pair, and the run stays on the same
-    trajectory up to rounding."""
+    """The tuner times real steps with 4 and 2 particles per thread, then at
+    unit sizes 2048..16384, then at sort intervals 4..32, keeps the fastest
+    shapes, and the run stays on the same trajectory up to rounding."""
     d = EARLY  # the pulse is in the foil from step ~50 on
     res = []
     for tune in (True, False):
@@ -221,14 +221,16 @@ def test_shape_tuner(picrr):
         g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
         g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
         if tune:
-            unit, interval, ms = g.tune_shapes(32)
-            assert unit in (2048, 4096, 8192, 16384) and interval in (4, 8, 16, 32) and np.all(ms > 0)
-            assert interval == (4, 8, 16, 32)[int(np.argmin(ms[4:]))]
+            unit, interval, w, ms = g.tune_shapes(8)
+            assert unit in (2048, 4096, 8192, 16384) and interval in (4, 8, 16, 32) and w in (2, 4)
+            assert np.all(ms > 0)
+            assert w == (4, 2)[int(np.argmin(ms[:2]))] and interval == (4, 8, 16, 32)[int(np.argmin(ms[6:]))]
             done = g.stats()["steps"]
-            assert done == 4 * (8 + 32) + 4 + 32 + 8 + 32 + 16 + 32 + 32 + 32
-            g.step(400 - done)
+            # warm-up interval + trial for each candidate (a trial is at least one interval)
+            assert done == 2 * (8 + 8) + 4 * (8 + 8) + (4 + 8) + (8 + 8) + (16 + 16) + (32 + 32)
+            g.step(300 - done)
         else:
-            g.step(400)
+            g.step(300)
         res.append([g.field(c) for c in range(5)])
         g.close()
     for c in range(5):
@@ -238,13 +240,13 @@ def test_shape_tuner(picrr):
 def test_set_shapes_changes_only_rounding(picrr):
     d = EARLY
     out = []
-    for unit, interval in ((1024, 8), (16384, 4), (4096, 16)):
+    for unit, interval, w in ((1024, 8, 4), (16384, 4, 2), (4096, 16, 2)):
         g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
                       seed=d["seed"])
         g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
         g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
         g.step(13)
-        g.set_shapes(unit, interval)  # mid-interval: sorted first
+        g.set_shapes(unit, interval, w)  # mid-interval: sorted first
         g.step(187)
         out.append((np.concatenate([g.field(c) for c in range(5)]), g.particles(0)))
         g.close()
@@ -253,4 +255,4 @@ def test_set_shapes_changes_only_rounding(picrr):
         assert np.max(np.abs(p["px"] - out[0][1]["px"])) <= 1e-3 * (1 + np.max(np.abs(out[0][1]["px"])))
     with pytest.raises(picrr.PicError):
         g = picrr.Sim(length_lambda=4, cells_per_lambda=CPL)
-        g.set_shapes(3000, 8)
+        g.set_shapes(3000, 8, 4)
