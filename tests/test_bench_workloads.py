@@ -1,0 +1,41 @@
+"""The benchmark's synthetic workloads have the shapes the growth plan states
+(host logic only, no GPU)."""
+import math
+
+import numpy as np
+
+import bench
+
+
+def test_scan_runs_follow_the_stated_distributions():
+    descs = [bench.scan_desc(i) for i in range(256)]
+    assert bench.scan_steps(40) == 21053  # 40 periods at lambda/500, dt = 0.95 dx
+    a0 = np.array([d["a0"] for d in descs])
+    th = np.array([d["foil_thickness"] for d in descs])
+    ne = np.array([d["ne"] for d in descs])
+    ppc = np.array([d["ppc"] for d in descs])
+    assert a0.min() >= 100 and a0.max() <= 600 and th.min() >= 0.5 and th.max() <= 2.0
+    assert ne.min() >= 30 and ne.max() <= 150 and ppc.min() >= 32 and ppc.max() <= 256
+    for key in ("polarization", "rr_on"):
+        frac = np.mean([bool(d[key]) for d in descs])
+        assert 0.35 < frac < 0.65  # 50/50
+    n = np.array([bench.desc_particles(d, 500) // 2 for d in descs])
+    assert 5_000 <= n.min() and n.max() <= 256_000  # about 5k..250k per species
+    assert all(d["length_lambda"] == 30.0 and d["foil_x0"] == 10.0 for d in descs)
+    assert len({d["seed"] for d in descs}) == 256
+    # deterministic
+    assert bench.scan_desc(17) == bench.scan_desc(17)
+
+
+def test_request_stream_is_poisson_with_log_uniform_sizes():
+    reqs = bench.serve_requests(20.0, 100.0, seed=5)
+    t = np.array([r[0] for r in reqs])
+    assert abs(len(reqs) - 2000) < 4 * math.sqrt(2000)  # Poisson count at 20/s over 100 s
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 0.05) < 0.005 and abs(gaps.std() / gaps.mean() - 1.0) < 0.1  # exponential gaps
+    n = np.array([bench.desc_particles(d, 500) / 2 for _, d in reqs])
+    assert n.min() > 0.7e4 and n.max() < 1.3e6
+    logn = np.log10(n)
+    assert abs(np.mean(logn) - 5.0) < 0.1  # log-uniform on [1e4, 1e6]
+    periods = np.array([d["steps"] for _, d in reqs]) * 0.95 / 500
+    assert periods.min() >= 20.0 - 1e-9 and periods.max() <= 200.0 + 0.01
