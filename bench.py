@@ -195,11 +195,12 @@ def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
     return _latency_summary(lat, [el - reqs[j][0] for j in pending if reqs[j][0] <= el], el, len(reqs))
 
 
-def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None):
+def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None, first=0):
     """All runs in one batch (one launch per kernel per step for all of them),
     from creation to every run's ion spectrum on the host.  max_steps (for
-    profiling) cuts every run short."""
-    descs = [scan_desc(i, w) for i in range(n_runs)]
+    profiling) cuts every run short; first: index of the first run (each rank
+    of a multi-GPU job takes its own runs)."""
+    descs = [scan_desc(first + i, w) for i in range(n_runs)]
     if max_steps:
         descs = [dict(d, steps=min(d["steps"], max_steps)) for d in descs]
     t0 = time.perf_counter()
@@ -220,10 +221,10 @@ def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None):
                 push_launches=st["push_launches"], kernel_launches=st["kernel_launches"])
 
 
-def plain_scan(picrr, device, n_runs, w=SCAN):
+def plain_scan(picrr, device, n_runs, w=SCAN, first=0):
     """The same runs one at a time through the single-run API (create, foil,
     laser, step to the end, ion spectrum, destroy), on the same GPU."""
-    descs = [scan_desc(i, w) for i in range(n_runs)]
+    descs = [scan_desc(first + i, w) for i in range(n_runs)]
     t0 = time.perf_counter()
     for d in descs:
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
@@ -517,9 +518,11 @@ def main():
 
     scan = None
     if args.scan_runs > 0:
-        scan = batched_scan(picrr, local, args.scan_runs, max_steps=args.scan_steps or None)
+        # weak scaling: rank r takes runs [r * n, (r + 1) * n) of the scan's seed sequence
+        scan = batched_scan(picrr, local, args.scan_runs, max_steps=args.scan_steps or None,
+                            first=rank * args.scan_runs)
         if args.plain_runs > 0:
-            plain = plain_scan(picrr, local, min(args.plain_runs, args.scan_runs))
+            plain = plain_scan(picrr, local, min(args.plain_runs, args.scan_runs), first=rank * args.scan_runs)
             scan["plain"] = plain
             scan["speedup_runs_per_hour"] = scan["runs_per_hour"] / plain["runs_per_hour"]
         scan["workload"] = ("%d runs, 15,000 cells (30 lambda, lambda/500), 21,053 steps each; a0 U[100,600], "
@@ -544,12 +547,13 @@ def main():
                                   cfg["cap_s"]))
             return out
 
+        # each rank of a multi-GPU job serves its own request stream (weak scaling); rank 0 reports its own
         cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
-                   policy=args.serve_policy, resident=args.serve_resident)
+                   policy=args.serve_policy, resident=args.serve_resident, seed=SERVE["seed"] + 1000 * rank)
         serving = one_stream(cfg)
         if args.serve_low_rate > 0:
             low = dict(SERVE_LOW, cap_s=args.serve_cap, rate=args.serve_low_rate, policy=args.serve_policy,
-                       resident=args.serve_resident)
+                       resident=args.serve_resident, seed=SERVE_LOW["seed"] + 1000 * rank)
             serving["sustainable_rate"] = one_stream(low)
 
     cpu = None
