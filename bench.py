@@ -44,7 +44,7 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles,
 # 16384 particles per unit, sort every 32 steps); reported when the run matches
 PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=32, particles_per_thread=4,
-                    bytes=1_280_281_856 + 1_219_174_912)
+                    bytes=1_280_350_208 + 1_219_191_808)
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
