@@ -186,7 +186,7 @@ typedef struct {
     int64_t kernel_launches;  /* device kernels launched by this handle */
     int64_t push_launches;    /* launches of the fused gather/push/deposit kernel */
     int64_t sort_count;       /* cell sorts performed */
-    int64_t active_particles; /* particles not frozen at a wall, both species */
+    int64_t active_particles; /* particles of the runs still stepping, both species (frozen ones included) */
     double push_ms;           /* summed device time of the push kernel (timing on) */
     double field_ms;          /* summed device time of the Yee kernel (timing on) */
     double sort_ms;           /* summed device time of the sort kernels (timing on) */
