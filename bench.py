@@ -19,6 +19,7 @@ plain C, single thread) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -255,19 +256,39 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler for the timed region."""
+    """nvidia-smi sampler (every 50 ms); only the samples stamped between
+    begin() and end() (the timed region) are kept."""
 
     def __init__(self, index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # let the sampler start before the timed region
+        for _ in range(40):
+            if self.p is None or os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
+
+    @staticmethod
+    def _stamp(text):
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f")
+        except ValueError:
+            return None
 
     def stop(self):
         if self.p is None:
@@ -281,6 +302,10 @@ class Clocks:
         self.f.seek(0)
         rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if (lambda t: t is not None and self.t0 <= t <= self.t1)(self._stamp(r[0]))]
+            if inside:
+                rows = inside
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -399,7 +424,7 @@ def e2e_run(picrr, torch, device, steps, host, shapes=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-steps", type=int, default=40)
@@ -484,10 +509,14 @@ def main():
     torch.cuda.synchronize()
     sim.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.begin()
     ev0.record(stream)
     sim.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    if clocks:
+        clocks.end()
     barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None

@@ -225,10 +225,12 @@ pic_status pic_tune_shapes(pic_sim* sim, int64_t steps_per_candidate, int* unit_
                            int* particles_per_thread, double* ms_per_step);
 
 /* Counters and, when timing is on, CUDA-event times of each kernel class,
- * recorded on the launching stream.  With timing off, every whole sort
- * interval of steps that no run ends inside is launched as one captured CUDA
- * graph (its pushes, Yee updates and the sort); with timing on, every kernel
- * is launched on its own so that it can be timed. */
+ * recorded on the launching stream.  Every whole sort interval of steps that
+ * no run ends inside is launched as one captured CUDA graph (its pushes, Yee
+ * updates and the sort); with timing on, that graph also holds an event-record
+ * node before and after each push, Yee update and sort, and the other steps
+ * record their events around each launch.  The times are read when a step
+ * call returns (and before a graph is launched again). */
 pic_status pic_stats(pic_sim* sim, pic_stats_t* out);
 pic_status pic_set_timing(pic_sim* sim, int on);
 

@@ -145,6 +145,13 @@ struct Batch {
     uint64_t epoch = 1;
     bool graphs_on = true;
     int64_t graph_launches = 0;
+    // With timing on, the graphs also hold event-record nodes around every
+    // push, Yee update and the sort: the event pairs of each graph, whether it
+    // was captured with them, and whether a launch of it has not been read yet
+    // (it is read before the same graph is launched again).
+    std::vector<EventPair> graph_ev[2][2];
+    bool graph_timed[2][2] = {};
+    bool graph_unread[2][2] = {};
 
     UnitTable units{};
     int max_units = 0;
@@ -283,23 +290,56 @@ struct Timed {
     }
 };
 
+void add_timing(Batch* b, const EventPair& ep) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ep.a, ep.b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (ep.kind == 0) {
+        b->push_ms += ms;
+        b->timed_push++;
+    } else if (ep.kind == 1) {
+        b->field_ms += ms;
+    } else {
+        b->sort_ms += ms;
+    }
+}
+
 void collect_timing(Batch* b) {
     for (EventPair& ep : b->pending) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ep.a, ep.b) == cudaSuccess) {
-            if (ep.kind == 0) {
-                b->push_ms += ms;
-                b->timed_push++;
-            } else if (ep.kind == 1) {
-                b->field_ms += ms;
-            } else {
-                b->sort_ms += ms;
-            }
-        }
+        add_timing(b, ep);
         b->ev_free.push_back(ep.a);
         b->ev_free.push_back(ep.b);
     }
     b->pending.clear();
+}
+
+// Times of the last launch of chunk graph [par0][cur] (waits for its last event).
+void read_graph_timing(Batch* b, int par0, int cur) {
+    if (!b->graph_unread[par0][cur]) return;
+    b->graph_unread[par0][cur] = false;
+    const std::vector<EventPair>& ev = b->graph_ev[par0][cur];
+    if (ev.empty() || cudaEventSynchronize(ev.back().b) != cudaSuccess) return;
+    for (const EventPair& ep : ev) add_timing(b, ep);
+}
+
+void read_all_graph_timing(Batch* b) {
+    for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < 2; ++c) read_graph_timing(b, p, c);
+}
+
+// Drop graph [par0][cur] and give its events back (after reading them).
+void drop_graph(Batch* b, int par0, int cur) {
+    read_graph_timing(b, par0, cur);
+    if (b->graph[par0][cur]) cudaGraphExecDestroy(b->graph[par0][cur]);
+    b->graph[par0][cur] = nullptr;
+    for (EventPair& ep : b->graph_ev[par0][cur]) {
+        b->ev_free.push_back(ep.a);
+        b->ev_free.push_back(ep.b);
+    }
+    b->graph_ev[par0][cur].clear();
+    b->graph_timed[par0][cur] = false;
 }
 
 // ---------------------------------------------------------------------------
@@ -397,9 +437,14 @@ void batch_destroy(Batch* b) {
         if (b->inc_ev[i]) cudaEventDestroy(b->inc_ev[i]);
     if (b->h_runs) cudaFreeHost(b->h_runs);
     if (b->h_inc) cudaFreeHost(b->h_inc);
-    for (auto& row : b->graph)
-        for (auto& g : row)
-            if (g) cudaGraphExecDestroy(g);
+    for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < 2; ++c) {
+            if (b->graph[p][c]) cudaGraphExecDestroy(b->graph[p][c]);
+            for (EventPair& ep : b->graph_ev[p][c]) {
+                cudaEventDestroy(ep.a);
+                cudaEventDestroy(ep.b);
+            }
+        }
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
@@ -1009,27 +1054,37 @@ FieldParams field_params(const Batch* b, int64_t gstep, int j) {
 // particle buffer cur (captured on the batch's capture stream, then reused).
 pic_status chunk_graph(Batch* b, int par0, int cur, cudaGraphExec_t* out) {
     cudaGraphExec_t& ex = b->graph[par0][cur];
-    if (ex && b->graph_epoch[par0][cur] == b->epoch) {
+    if (ex && b->graph_epoch[par0][cur] == b->epoch && b->graph_timed[par0][cur] == b->timing) {
         *out = ex;
         return PIC_OK;
     }
-    if (ex) {
-        cudaGraphExecDestroy(ex);
-        ex = nullptr;
-    }
+    drop_graph(b, par0, cur);
     const int I = b->sort_interval;
     cudaStream_t cs = b->cap_stream;
+    std::vector<EventPair>& ev = b->graph_ev[par0][cur];
+    // timing on: an event-record node before and after each timed launch
+    auto mark = [&](int kind, bool open) {
+        if (!b->timing) return;
+        if (open) ev.push_back(EventPair{take_event(b), take_event(b), kind});
+        cudaEventRecordWithFlags(open ? ev.back().a : ev.back().b, cs, cudaEventRecordExternal);
+    };
     PIC_CK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int j = 0; j < I; ++j) {
+        mark(0, true);
         launch_push(push_params(b, par0 + j, j, cur), b->max_units, b->slot_w, cs);
+        mark(0, false);
+        mark(1, true);
         launch_field(field_params(b, par0 + j, j), b->nblk, cs);
+        mark(1, false);
     }
+    mark(2, true);
     launch_rad_flush(b->d_runs, b->max_runs, b->rs_units, b->rad_part, cs);
     SortParams S = sort_params(b);
     S.k = I;
     S.cur = cur;
     int nl = 0;
     launch_sort(S, cs, &nl);
+    mark(2, false);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
@@ -1039,6 +1094,7 @@ pic_status chunk_graph(Batch* b, int par0, int cur, cudaGraphExec_t* out) {
         return cuda_fail(b, e, "chunk graph");
     }
     b->graph_epoch[par0][cur] = b->epoch;
+    b->graph_timed[par0][cur] = b->timing;
     *out = ex;
     return PIC_OK;
 }
@@ -1053,7 +1109,7 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
     int64_t it = 0;
     while (it < n) {
         int nact = 0;
-        bool whole_chunk = b->graphs_on && !b->timing && b->since_sort == 0 && n - it >= I;
+        bool whole_chunk = b->graphs_on && b->since_sort == 0 && n - it >= I;
         for (auto& r : b->runs) {
             if (!r.used || !r.active) continue;
             nact++;
@@ -1063,9 +1119,12 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
         if (whole_chunk) {
             // a whole sort interval as one graph launch; no run ends before its last step
             cudaGraphExec_t ex = nullptr;
-            if ((st = chunk_graph(b, static_cast<int>(b->gstep & 1), b->cur, &ex)) != PIC_OK) return st;
+            const int gp = static_cast<int>(b->gstep & 1), gc = b->cur;
+            if ((st = chunk_graph(b, gp, gc, &ex)) != PIC_OK) return st;
             if ((st = upload_incident(b, I)) != PIC_OK) return st;
+            read_graph_timing(b, gp, gc);  // its previous launch (two chunks ago), before its events are reused
             PIC_CK(b, cudaGraphLaunch(ex, b->stream));
+            b->graph_unread[gp][gc] = b->timing;
             b->graph_launches++;
             b->launches += 2 * I + 1 + 8;
             b->push_launches += I;
@@ -1132,6 +1191,7 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(b, e, "step");
     collect_timing(b);
+    read_all_graph_timing(b);
     int hst = 0;
     PIC_CK(b, cudaMemcpy(&hst, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (done) *done = it;
@@ -1642,6 +1702,7 @@ pic_status set_timing(Batch* b, int on) {
     DeviceGuard g(b->device);
     cudaStreamSynchronize(b->stream);
     collect_timing(b);
+    read_all_graph_timing(b);
     b->timing = on != 0;
     if (b->timing) {
         b->push_ms = b->field_ms = b->sort_ms = 0.0;

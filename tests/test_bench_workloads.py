@@ -39,3 +39,28 @@ def test_request_stream_is_poisson_with_log_uniform_sizes():
     assert abs(np.mean(logn) - 5.0) < 0.1  # log-uniform on [1e4, 1e6]
     periods = np.array([d["steps"] for _, d in reqs]) * 0.95 / 500
     assert periods.min() >= 20.0 - 1e-9 and periods.max() <= 200.0 + 0.01
+
+
+def test_clock_samples_are_kept_only_inside_the_timed_region(tmp_path):
+    import datetime
+
+    c = bench.Clocks.__new__(bench.Clocks)  # no sampler process: feed a recorded trace
+    rows = ["2026/12/03 03:12:55.000, 1400, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "2026/12/03 03:12:55.100, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "2026/12/03 03:12:55.150, 2070, 2070, 1250.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "2026/12/03 03:12:55.400, 1200, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    f = open(tmp_path / "clk.csv", "w+")
+    f.write("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c.f, c.p = f, Done()
+    c.t0 = datetime.datetime(2026, 12, 3, 3, 12, 55, 50000)
+    c.t1 = datetime.datetime(2026, 12, 3, 3, 12, 55, 300000)
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}

@@ -189,24 +189,39 @@ def test_batch_argument_errors(picrr):
 
 
 def test_graph_chunks_equal_single_launches(picrr):
-    """With timing off, whole sort intervals run as one captured CUDA graph;
-    with timing on, every kernel is launched on its own.  Same results."""
+    """Whole sort intervals run as one captured CUDA graph; step calls shorter
+    than an interval launch every kernel on its own; with timing on, the graphs
+    carry event-record nodes that time every push, Yee update and sort.  Same
+    results in all three modes."""
     d = RUNS[0]
     out, st = [], []
-    for timing in (False, True):
+    for mode in ("graphs", "single", "graphs+timing"):
         g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
                       seed=d["seed"])
         g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
         g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
-        g.set_timing(timing)
-        for n in (5, 3, 200, d["steps"] - 208):  # chunks start only on sort boundaries
-            g.step(n)
+        g.set_timing(mode == "graphs+timing")
+        if mode == "single":
+            left = d["steps"]
+            while left > 0:  # calls of fewer steps than a sort interval never form a graph chunk
+                g.step(min(7, left))
+                left -= 7
+        else:
+            for n in (5, 3, 200, d["steps"] - 208):  # chunks start only on sort boundaries
+                g.step(n)
         out.append(snapshot(g.particles, g.field, g.energy, g.spectra))
         st.append(g.stats())
         g.close()
-    assert st[0]["graph_launches"] == (d["steps"] - 8) // 8 and st[1]["graph_launches"] == 0
-    assert st[0]["kernel_launches"] == st[1]["kernel_launches"]
+    chunks = (d["steps"] - 8) // 8
+    assert st[0]["graph_launches"] == chunks and st[1]["graph_launches"] == 0 and st[2]["graph_launches"] == chunks
+    # (each short step call also flushes the radiated-energy partials: one launch more)
+    assert st[0]["kernel_launches"] == st[2]["kernel_launches"] <= st[1]["kernel_launches"]
+    # every push of the timed run was timed, inside the graphs as well as outside
+    assert st[2]["timed_push_launches"] == st[2]["push_launches"] == d["steps"]
+    assert st[2]["push_ms"] > 0 and st[2]["field_ms"] > 0 and st[2]["sort_ms"] > 0
+    assert st[0]["timed_push_launches"] == 0
     assert_same(out[0], out[1], "graph vs single launches")
+    assert_same(out[0], out[2], "graph vs timed graph")
 
 
 def test_shape_tuner(picrr):
