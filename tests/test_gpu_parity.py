@@ -83,6 +83,38 @@ def test_one_step_random_particles_and_fields(picrr, rr):
         assert eg[3] == pytest.approx(eo[3], rel=1e-4)
 
 
+@pytest.mark.parametrize("ppt", [2, 4])
+def test_one_step_dense_tiles_split_into_units(picrr, ppt):
+    """Dense cells (about 250 particles each): every 64-cell tile splits into
+    units of 1024 particles whose ends fall inside the slots of 2 or 4
+    particles a thread takes, so the partial-slot loads and stores at unit
+    boundaries and the merged warp records of crowded cells are all on the
+    path; one step against the oracle."""
+    g, o = pair(picrr, length_lambda=4, cells_per_lambda=100, rr_on=True)
+    nx = g.nx
+    F = synth.random_fields(nx, scale=80.0, seed=6)
+    for s in (g, o):
+        s.set_fields(*F)
+    for sp, (n, q, m, w) in enumerate([(20011, -1.0, 1.0, 0.002), (19997, 1.0, 1836.15267343, 0.002)]):
+        cell, off, px, py, pz = synth.random_particles(n, 150, 230, pscale=60.0 if sp == 0 else 2.0, seed=20 + sp)
+        for s in (g, o):
+            s.load_particles(sp, cell, off, px, py, pz, w, q, m)
+    g.set_shapes(1024, 8, ppt)
+    assert g.stats()["n_units"] >= 2 * (20000 // 1024)  # both species split into many units
+    g.step(1)
+    o.step(1)
+    for sp in (0, 1):
+        pg, po = g.particles(sp), o.particles(sp)
+        check_momenta(pg, po, 80.0, g.dt)
+        assert np.max(np.abs(pg["x"] - po["x"])) <= 2e-6 * g.dx
+        assert np.array_equal(pg["flag"], po["flag"])
+    for comp in range(8):
+        a, b = g.field(comp), o.field(comp)
+        assert rel_l2(a, b) <= 2e-6, comp
+    eg, eo = g.energy(), o.energy()
+    assert eg[3] == pytest.approx(eo[3], rel=1e-4)
+
+
 def laser_foil_pair(picrr, rr=True, pol=0, a0=200.0, ne=64.0, ppc=32, sort_interval=8, seed=7):
     g, o = pair(picrr, seed=seed, sort_interval=sort_interval, length_lambda=3, cells_per_lambda=200,
                 rr_on=rr)
