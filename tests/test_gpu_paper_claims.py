@@ -12,7 +12,12 @@ species (the paper's resolution is not given).  Claims checked:
 - LP: d reaches about 1e2 at t = 1.6-1.7 T, up to four orders of magnitude
   above CP; a sizeable fraction of the pulse energy is radiated (the paper
   reports about 20 %); with RR the ion spectrum at 12 T has a lower peak
-  energy and a smaller spread.
+  energy and a smaller spread.  The LP runs are chaotic: over four seeds and
+  two work-unit groupings the maximum of the smoothed spectrum of one run
+  moved between 485 and 745 MeV, while the median ion energy (the bulk of the
+  spectrum) stayed within 535-565 MeV with RR and 635-685 MeV without, and the
+  spread within 145-175 and 261-288 MeV.  The lower peak energy is therefore
+  checked on the median.
 
 The bands are wide on purpose: the claims are qualitative, and the paper's
 grid, particle numbers and diagnostics are not given.
@@ -54,7 +59,9 @@ def runs():
                     e = (np.arange(400) + 0.5) * 10.0
                     sm = np.convolve(c, np.ones(9) / 9, "same")
                     mean = c @ e / c.sum()
-                    r["ion"] = dict(peak=e[np.argmax(sm)], mean=mean, std=math.sqrt(c @ (e - mean) ** 2 / c.sum()))
+                    cum = np.cumsum(c)
+                    r["ion"] = dict(peak=e[np.argmax(sm)], mean=mean, std=math.sqrt(c @ (e - mean) ** 2 / c.sum()),
+                                    median=e[np.searchsorted(cum, 0.5 * cum[-1])])
                 rec[tag] = r
             g.close()
             out[name + ("_RR" if rr else "_noRR")] = rec
@@ -80,5 +87,5 @@ def test_lp_friction_large_and_rr_matters(runs):
     frac = lp["30"]["energy"][3] / U_PULSE
     assert 0.05 < frac < 0.4  # "about 20 % of the pulse energy lost as incoherent radiation"
     a, b = lp["12"]["ion"], runs["LP_noRR"]["12"]["ion"]
-    assert a["peak"] < b["peak"]  # lower peak energy with RR
-    assert a["std"] < b["std"]  # smaller spread with RR
+    assert a["median"] < 0.95 * b["median"]  # lower energy of the spectrum's bulk with RR
+    assert a["std"] < 0.8 * b["std"]  # smaller spread with RR
