@@ -356,7 +356,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "large single run sample (oracle)", "cells": 200000},
+            "config": {"workload": large_workload(), "cells": 200000},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -374,6 +374,13 @@ def aggregate(torch, dist, ms, particle_steps):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(n, op=dist.ReduceOp.SUM)
     return float(t.item()), float(n.item())
+
+
+def large_workload(ppc=LARGE["ppc"]):
+    """The name of the large single run (both arms report the same workload)."""
+    n = ppc * int(round(LARGE["foil_thickness"] * LARGE["cells_per_lambda"]))
+    return ("large single run: 200,000 cells (100 lambda, lambda/2000), 2-lambda H foil n_e=100 n_c, "
+            "%d ppc/species (%.3gM e + %.3gM p), CP a0=500, RR on" % (ppc, n / 1e6, n / 1e6))
 
 
 def make_sim(picrr, device, w=LARGE):
@@ -595,8 +602,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "large single run: 200,000 cells (100 lambda, lambda/2000), 2-lambda H foil "
-                                   "n_e=100 n_c, 8000 ppc/species (32M e + 32M p), CP a0=500, RR on",
+            "config": {"workload": large_workload(args.ppc),
                        "particles": n_active, "particles_end": n_active_end, "cells": 200000,
                        "sort_interval": shapes["sort_interval"] if shapes else w["sort_interval"],
                        "shapes": shapes,
