@@ -44,8 +44,8 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # DRAM traffic of one push launch of this workload, measured with ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles,
 # 16384 particles per unit, sort every 32 steps); reported when the run matches
-PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=32, particles_per_thread=4,
-                    bytes=1_280_350_208 + 1_219_191_808)
+PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=64, particles_per_thread=4,
+                    bytes=1_280_280_320 + 1_218_965_248)
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
@@ -495,7 +495,7 @@ def main():
         shapes = {"unit_particles": unit, "sort_interval": interval, "particles_per_thread": ppt, "tuned": True,
                   "trial_ms_per_step": {"particles_per_thread_4_2": [round(v, 4) for v in tms[:2]],
                                         "unit_2048_4096_8192_16384": [round(v, 4) for v in tms[2:6]],
-                                        "interval_4_8_16_32": [round(v, 4) for v in tms[6:]]}}
+                                        "interval_8_16_32_64": [round(v, 4) for v in tms[6:]]}}
     sim = make_sim(picrr, local)
     sim.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
     sim.inject_laser(w["a0"], w["pol"], 0, w["duration"])

@@ -353,7 +353,7 @@ pic_status validate_common(const pic_config* cfg) {
     if (!(cfg->cfl > 0.0 && cfg->cfl < 1.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfl must be in (0, 1)");
     if (!(cfg->lambda_um > 0.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "lambda_um must be > 0");
     if (cfg->sort_interval < 0 || cfg->sort_interval > KMAX)
-        return fail(nullptr, PIC_ERR_INVALID_ARG, "sort_interval must be in [0, 32]");
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "sort_interval must be in [0, 64]");
     return PIC_OK;
 }
 
@@ -1219,7 +1219,7 @@ pic_status set_shapes(Batch* b, int unit_p, int interval, int slot_w) {
     if (unit_p < UNIT_P_MIN || unit_p > UNIT_P_MAX || (unit_p & (unit_p - 1)) != 0)
         return fail(b, PIC_ERR_INVALID_ARG, "unit size must be a power of two in [1024, 16384]");
     if (slot_w != 2 && slot_w != 4) return fail(b, PIC_ERR_INVALID_ARG, "particles per thread must be 2 or 4");
-    if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 32]");
+    if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 64]");
     pic_status st = activate_pending(b);
     if (st != PIC_OK) return st;
     bool any = false;
@@ -1256,7 +1256,7 @@ pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval
                        double* ms_out) {
     static const int slots[2] = {4, 2};
     static const int units[4] = {2048, 4096, 8192, 16384};
-    static const int cand[4] = {4, 8, 16, 32};
+    static const int cand[4] = {8, 16, 32, 64};
     if (steps_per < 1) return fail(b, PIC_ERR_INVALID_ARG, "steps_per_candidate must be >= 1");
     if (b->timing) return fail(b, PIC_ERR_STATE, "turn timing off before tuning");
     if (ms_out)

@@ -36,7 +36,7 @@ constexpr int SPAN = GROUP * TILE;  // cell span bound of a unit
 constexpr int UNIT_P = 4096;      // default particles per unit at most (unit_p, a run-time shape of a batch)
 constexpr int UNIT_P_MIN = 1024;  // smallest unit_p (the bound used for memory estimates)
 constexpr int UNIT_P_MAX = 16384;
-constexpr int KMAX = 32;          // largest sort interval
+constexpr int KMAX = 64;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
 constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push kernel (>= SPAN + 2 KMAX + 9)
 constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)

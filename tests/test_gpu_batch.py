@@ -226,7 +226,7 @@ def test_graph_chunks_equal_single_launches(picrr):
 
 def test_shape_tuner(picrr):
     """The tuner times real steps with 4 and 2 particles per thread, then at
-    unit sizes 2048..16384, then at sort intervals 4..32, keeps the fastest
+    unit sizes 2048..16384, then at sort intervals 8..64, keeps the fastest
     shapes, and the run stays on the same trajectory up to rounding."""
     d = EARLY  # the pulse is in the foil from step ~50 on
     res = []
@@ -237,15 +237,15 @@ def test_shape_tuner(picrr):
         g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
         if tune:
             unit, interval, w, ms = g.tune_shapes(8)
-            assert unit in (2048, 4096, 8192, 16384) and interval in (4, 8, 16, 32) and w in (2, 4)
+            assert unit in (2048, 4096, 8192, 16384) and interval in (8, 16, 32, 64) and w in (2, 4)
             assert np.all(ms > 0)
-            assert w == (4, 2)[int(np.argmin(ms[:2]))] and interval == (4, 8, 16, 32)[int(np.argmin(ms[6:]))]
+            assert w == (4, 2)[int(np.argmin(ms[:2]))] and interval == (8, 16, 32, 64)[int(np.argmin(ms[6:]))]
             done = g.stats()["steps"]
             # warm-up interval + trial for each candidate (a trial is at least one interval)
-            assert done == 2 * (8 + 8) + 4 * (8 + 8) + (4 + 8) + (8 + 8) + (16 + 16) + (32 + 32)
-            g.step(300 - done)
+            assert done == 2 * (8 + 8) + 4 * (8 + 8) + (8 + 8) + (16 + 16) + (32 + 32) + (64 + 64)
+            g.step(340 - done)
         else:
-            g.step(300)
+            g.step(340)
         res.append([g.field(c) for c in range(5)])
         g.close()
     for c in range(5):
@@ -255,7 +255,7 @@ def test_shape_tuner(picrr):
 def test_set_shapes_changes_only_rounding(picrr):
     d = EARLY
     out = []
-    for unit, interval, w in ((1024, 8, 4), (16384, 4, 2), (4096, 16, 2)):
+    for unit, interval, w in ((1024, 8, 4), (16384, 4, 2), (4096, 16, 2), (16384, 64, 4)):
         g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
                       seed=d["seed"])
         g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
