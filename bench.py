@@ -42,10 +42,13 @@ LARGE = dict(length_lambda=100.0, cells_per_lambda=2000.0, cfl=0.95, lambda_um=0
              duration=20.0, seed=4, sort_interval=8)
 BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int32 + 4 x fp32)
 # DRAM traffic of one push launch of this workload, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles,
-# 16384 particles per unit, sort every 32 steps); reported when the run matches
-PUSH_TRAFFIC = dict(particles=64_000_000, unit_particles=16384, sort_interval=64, particles_per_thread=4,
-                    bytes=1_280_280_320 + 1_218_965_248)
+# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles) for
+# the launch shapes the tuner picks for it, keyed by (particles, particles per
+# unit, sort interval, particles per thread); reported when the run matches
+PUSH_TRAFFIC = {
+    (64_000_000, 16384, 64, 4): 1_280_280_320 + 1_218_965_248,
+    (64_000_000, 16384, 32, 4): 1_280_300_032 + 1_218_996_992,
+}
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
@@ -536,10 +539,9 @@ def main():
     achieved = BYTES_PER_PARTICLE_STEP * n_active / (push_avg_ms / 1e3) / 1e9
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     traffic = None
-    if (shapes and n_active == PUSH_TRAFFIC["particles"] and shapes["unit_particles"] == PUSH_TRAFFIC["unit_particles"]
-            and shapes["sort_interval"] == PUSH_TRAFFIC["sort_interval"]
-            and shapes["particles_per_thread"] == PUSH_TRAFFIC["particles_per_thread"]):
-        traffic = PUSH_TRAFFIC["bytes"]
+    if shapes:
+        traffic = PUSH_TRAFFIC.get((n_active, shapes["unit_particles"], shapes["sort_interval"],
+                                    shapes["particles_per_thread"]))
     sim.close()
 
     e2e = None
