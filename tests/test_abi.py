@@ -61,3 +61,41 @@ def test_destroy_null_and_null_handle_calls(lib):
     out = C.c_void_p()
     assert lib.pic_create(None, C.byref(out)) == -1 and not out.value
     assert b"NULL" in lib.pic_last_error(None)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout: a small C
+    program built with the host compiler prints every field's offset and each
+    struct's size, compared with the binding's."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_1008_1685_gb300 import binding as B
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pic_config": B.Config, "pic_run_desc": B.RunDesc, "pic_stats_t": B.Stats,
+               "pic_server_stats_t": B.ServerStats, "pic_electron_case": B.ElectronCase}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "picrr.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            cname, field, value = line.split()
+            got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -64,3 +64,12 @@ def test_clock_samples_are_kept_only_inside_the_timed_region(tmp_path):
     c.t1 = datetime.datetime(2026, 12, 3, 3, 12, 55, 300000)
     out = c.stop()
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+
+
+def test_both_arms_name_the_same_workload_and_traffic_is_keyed_by_shapes():
+    assert "8000 ppc/species (32M e + 32M p)" in bench.large_workload()
+    assert "1000 ppc/species (4M e + 4M p)" in bench.large_workload(1000)
+    # measured DRAM bytes of one push launch stay close to the 40 B per particle-step the roofline counts
+    for (n, unit, interval, w), b in bench.PUSH_TRAFFIC.items():
+        assert n == 64_000_000 and w in (2, 4) and 1 <= interval <= 64 and unit in (2048, 4096, 8192, 16384)
+        assert 0.95 < b / (bench.BYTES_PER_PARTICLE_STEP * n) < 1.05
