@@ -195,6 +195,9 @@ typedef struct {
     int32_t n_units;          /* current work units (sorted particle chunks) */
     int32_t fp_bits;          /* fixed-point fraction bits of the current accumulators */
     int64_t graph_launches;   /* CUDA-graph launches, each one sort interval of steps */
+    int32_t steps_since_sort; /* steps since the last cell sort (the next sort comes after
+                                 sort_interval - steps_since_sort more steps) */
+    int32_t reserved;
 } pic_stats_t;
 
 /* Launch shapes.  unit_particles: the most particles one CTA of the fused
@@ -233,6 +236,15 @@ pic_status pic_tune_shapes(pic_sim* sim, int64_t steps_per_candidate, int* unit_
  * call returns (and before a graph is launched again). */
 pic_status pic_stats(pic_sim* sim, pic_stats_t* out);
 pic_status pic_set_timing(pic_sim* sim, int on);
+
+/* Switch the radiation-reaction kick of the electrons (Sec. 3, Eqs. f_r and
+ * pertfull) on (1) or off (0) from the next step on; the rest of the state is
+ * kept.  With it off the push is the Boris pusher alone.  It exists to
+ * measure what the kick costs on one and the same state (the paper puts the
+ * extra computing time at about 10 %, Sec. 3 last paragraph); the kick is
+ * evaluated for every electron whenever it is on, whatever the field.
+ * PIC_ERR_INVALID_ARG unless rr_on is 0 or 1. */
+pic_status pic_set_rr(pic_sim* sim, int rr_on);
 
 /* Message for the last failed call on sim (or on creation when sim is NULL,
  * for the calling thread).  Valid until the next call on the handle. */

@@ -36,7 +36,7 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_batch_tune_shapes", "pic_set_shapes", "pic_batch_set_shapes", "pic_server_set_policy",
            "pic_snapshot", "pic_batch_snapshot",
            "pic_electron_scan", "pic_selftest_wait_timeout", "pic_batch_stop_run", "pic_server_cancel",
-           "pic_save", "pic_restore", "pic_get_config")
+           "pic_save", "pic_restore", "pic_get_config", "pic_set_rr")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -115,6 +115,8 @@ class Stats(C.Structure):
         ("n_units", C.c_int32),
         ("fp_bits", C.c_int32),
         ("graph_launches", C.c_int64),
+        ("steps_since_sort", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
@@ -197,6 +199,7 @@ def library():
         L.pic_save.argtypes = [vp, C.c_char_p]
         L.pic_restore.argtypes = [C.c_char_p, C.c_int, C.c_int, C.POINTER(vp)]
         L.pic_get_config.argtypes = [vp, C.POINTER(Config)]
+        L.pic_set_rr.argtypes = [vp, C.c_int]
         L.pic_server_cancel.argtypes = [vp, i64]
         L.pic_snapshot.argtypes = [vp, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp, C.POINTER(i64)]
         L.pic_batch_snapshot.argtypes = [vp, C.c_int, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp,
@@ -416,6 +419,10 @@ class Sim:
 
     def set_shapes(self, unit_particles, sort_interval, particles_per_thread=2):
         self._check(self._L.pic_set_shapes(self._h, unit_particles, sort_interval, particles_per_thread))
+
+    def set_rr(self, on):
+        """Radiation-reaction kick of the electrons on or off from the next step (pic_set_rr)."""
+        self._check(self._L.pic_set_rr(self._h, int(on)))
 
     def set_timing(self, on=True):
         self._check(self._L.pic_set_timing(self._h, int(on)))

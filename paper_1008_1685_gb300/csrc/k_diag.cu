@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(DIAG_T) k_spectrum(DevSpecies sp, int64_t n, d
             k = nbins;
         } else {
             const double kf = floor((e - e_min) / (e_max - e_min) * static_cast<double>(nbins));
-            k = kf >= static_cast<double>(nbins) ? nbins + 1 : static_cast<int>(kf);
+            // written so that a NaN energy (never produced by a checked state) lands in the overflow
+            k = kf < static_cast<double>(nbins) ? static_cast<int>(kf) : nbins + 1;
         }
         if (use_sh) atomicAdd(&sh[k], 1u);
         else atomicAdd(&bins[k], 1ull);

@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(256) k_noalloc_count(const float* px, const fl
             k = nbins;
         } else {
             const double kf = floor((e - e_min) / (e_max - e_min) * static_cast<double>(nbins));
-            k = kf >= static_cast<double>(nbins) ? nbins + 1 : static_cast<int>(kf);
+            // written so that a NaN energy (never produced by a checked state) lands in the overflow
+            k = kf < static_cast<double>(nbins) ? static_cast<int>(kf) : nbins + 1;
         }
         atomicAdd(&bins[k], 1ull);
     }
@@ -95,7 +96,7 @@ extern "C" pic_status pic_spectrum_noalloc(const float* px, const float* py, con
         return noalloc_fail(PIC_ERR_INVALID_ARG, "need e_max > e_min (finite), mass > 0, finite weight");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return noalloc_fail(PIC_ERR_CUDA, "no current CUDA device");
     }

@@ -124,11 +124,14 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
     const int start = P.units.start[u], end = P.units.end[u];
     const int lo = P.units.lo[u], hi = P.units.hi[u];
     const int k = P.k;
-    const int w0 = lo - k - 1, w1 = hi + k + 3;
+    // cells [lo - k, hi + k] plus one neighbour left and two right; particles
+    // never leave [0, Nx - 1] (frozen ones are skipped), so the window is also
+    // clipped to the grid's cells -1 .. Nx + 1, which the guard elements hold
+    const int w0 = max(lo - k - 1, -1), w1 = min(hi + k + 3, R.Nx + 2);
     const int p0 = (w0 + PADF) & ~3;
     const int p1 = (w1 + PADF + 3) & ~3;
     const int L = p1 - p0;
-    if (L > WMAX || p0 < 0) {  // cannot happen for a valid unit table; never index out of the window
+    if (L > WMAX || p0 < 0 || p1 > R.glen) {  // cannot happen for a valid unit table; never copy out of the arrays
         if (tid == 0) atomicOr(P.status, ST_WINDOW);
         return;
     }

@@ -1683,6 +1683,7 @@ void fill_stats(Batch* b, pic_stats_t* out) {
     out->sort_ms = b->sort_ms;
     out->timed_push_launches = b->timed_push;
     out->graph_launches = b->graph_launches;
+    out->steps_since_sort = b->since_sort;
     out->device_bytes = static_cast<int64_t>(b->bytes);
     int64_t act = 0;
     int fp = 0;
@@ -1891,6 +1892,16 @@ pic_status pic_stats(pic_sim* s, pic_stats_t* out) {
 pic_status pic_set_timing(pic_sim* s, int on) {
     if (!s) return PIC_ERR_INVALID_ARG;
     return set_timing(s->b, on);
+}
+
+pic_status pic_set_rr(pic_sim* s, int rr_on) {
+    if (!s) return PIC_ERR_INVALID_ARG;
+    if (rr_on != 0 && rr_on != 1) return fail(s->b, PIC_ERR_INVALID_ARG, "rr_on must be 0 or 1");
+    RunHost& r = s->b->runs[0];
+    r.rr = rr_on;
+    r.dev.rr = rr_on;  // the kernels read the run table at run time: no graph recapture
+    s->b->table_dirty = true;
+    return PIC_OK;
 }
 
 const char* pic_last_error(const pic_sim* s) { return s ? s->b->err.c_str() : g_null_error.c_str(); }

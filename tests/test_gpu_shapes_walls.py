@@ -1,0 +1,171 @@
+"""GPU parity at the launch shapes the benchmark runs, and near the walls.
+
+- sort interval 64 (the largest) with electrons that reach and freeze at both
+  walls: the field windows of units next to a wall, staged 63 steps after a
+  sort, stay inside the grid arrays; particles, flags and fields against the
+  oracle;
+- the benchmark's tuned shapes (16384 particles per unit, 4 particles per
+  thread, sort every 64 steps) on a dense foil of 2M particles that fills
+  many units: every particle and all 8 grid components against the oracle
+  after 64 steps (windows k = 0 .. 63 steps after a sort), and after one step;
+- pic_set_rr switches the radiation-reaction kick on one and the same run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def picrr():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1008_1685_gb300 as m
+
+    return m
+
+
+def pair(picrr, seed=1, sort_interval=8, **kw):
+    kw.setdefault("cfl", 0.95)
+    kw.setdefault("lambda_um", 0.8)
+    kw.setdefault("source_node", 8)
+    g = picrr.Sim(seed=seed, sort_interval=sort_interval, **kw)
+    o = oracle.OracleSim(**kw)
+    return g, o
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def momentum_err(pg, po, fscale, dt):
+    """Per particle max-norm difference relative to max(|p|, 1e-3 F dt)."""
+    p_g = np.stack([pg["px"], pg["py"], pg["pz"]], 1)
+    p_o = np.stack([po["px"], po["py"], po["pz"]], 1)
+    scale = np.maximum(np.linalg.norm(p_o, axis=1), 1e-3 * fscale * dt)
+    return np.max(np.abs(p_g - p_o), axis=1) / scale
+
+
+def two_walls(n, nx, width, pscale, seed):
+    """n particles in the first and the last `width` cells of the box."""
+    a = synth.random_particles(n // 2, 0, width, pscale, seed)
+    b = synth.random_particles(n - n // 2, nx - width, nx, pscale, seed + 1)
+    return [np.concatenate([x, y]) for x, y in zip(a, b)]
+
+
+@pytest.mark.parametrize("shapes", [(1024, 64, 2), (16384, 64, 4)])
+def test_sort_interval_64_with_particles_frozen_at_both_walls(picrr, shapes):
+    g, o = pair(picrr, length_lambda=2, cells_per_lambda=100)
+    nx = g.nx
+    for sp, (n, q, m, w, ps) in enumerate([(3001, -1.0, 1.0, 0.002, 30.0), (2999, 1.0, 1836.15267343, 0.002, 0.5)]):
+        cell, off, px, py, pz = two_walls(n, nx, 20, ps, 40 + sp)
+        for s in (g, o):
+            s.load_particles(sp, cell, off, px, py, pz, w, q, m)
+    for s in (g, o):
+        s.inject_laser(20.0, picrr.LP, picrr.ENV_SIN2, 1.0)
+    g.set_shapes(*shapes)
+    g.step(130)  # sorts after steps 64 and 128; the pushes of steps 41..64 and 105..128 stage k >= 40
+    o.step(130)
+    pg, po = g.particles(0), o.particles(0)
+    assert np.array_equal(pg["flag"], po["flag"])
+    assert np.sum(pg["flag"] == -1) > 100 and np.sum(pg["flag"] == 1) > 100  # both walls hold frozen electrons
+    frozen = pg["flag"] != 0
+    assert np.all(pg["x"][pg["flag"] == -1] == 0.0) and np.all(pg["x"][pg["flag"] == 1] == nx * g.dx)
+    err = momentum_err(pg, po, 20.0, g.dt)
+    assert np.max(err) <= 1e-4, np.max(err)
+    # positions integrate the momenta over 130 steps (measured: 1.4e-4 cells)
+    assert np.max(np.abs(pg["x"] - po["x"])[~frozen]) <= 1e-3 * g.dx
+    for comp in range(5):
+        assert rel_l2(g.field(comp), o.field(comp)) <= 1e-4, comp
+    assert g.stats()["sort_count"] == 2
+
+
+def dense_foil_pair(picrr):
+    g, o = pair(picrr, length_lambda=5, cells_per_lambda=200, rr_on=True)
+    nx = g.nx
+    F = synth.random_fields(nx, scale=40.0, seed=8)
+    for s in (g, o):
+        s.set_fields(*F)
+    # about 2500 particles per cell per species in cells 300..700: 62 units of
+    # at most 16384 particles per species, each spanning about 7 cells
+    for sp, (n, q, m, w, ps) in enumerate([(1_000_003, -1.0, 1.0, 0.002, 30.0),
+                                           (999_997, 1.0, 1836.15267343, 0.002, 1.0)]):
+        cell, off, px, py, pz = synth.random_particles(n, 300, 700, pscale=ps, seed=30 + sp)
+        for s in (g, o):
+            s.load_particles(sp, cell, off, px, py, pz, w, q, m)
+    g.set_shapes(16384, 64, 4)
+    return g, o
+
+
+def test_tuned_shapes_dense_foil_one_step(picrr):
+    g, o = dense_foil_pair(picrr)
+    assert g.stats()["n_units"] >= 120
+    g.step(1)
+    o.step(1)
+    for sp in (0, 1):
+        pg, po = g.particles(sp), o.particles(sp)
+        assert np.max(momentum_err(pg, po, 40.0, g.dt)) <= 1e-5
+        assert np.max(np.abs(pg["x"] - po["x"])) <= 2e-6 * g.dx
+        assert np.array_equal(pg["flag"], po["flag"])
+    for comp in range(8):
+        assert rel_l2(g.field(comp), o.field(comp)) <= 2e-6, comp
+
+
+def test_tuned_shapes_dense_foil_through_a_whole_sort_interval(picrr):
+    """64 steps at sort interval 64: the last push stages windows 63 steps
+    wide on each side of its units (electrons with |p| ~ 30 cross up to 60
+    cells in that time); every particle and all 8 grid components (the
+    current of step 64) against the oracle."""
+    g, o = dense_foil_pair(picrr)
+    g.step(64)
+    o.step(64)
+    assert g.stats()["sort_count"] == 1
+    worst = {}
+    for sp in (0, 1):
+        pg, po = g.particles(sp), o.particles(sp)
+        worst["p%d" % sp] = float(np.max(momentum_err(pg, po, 40.0, g.dt)))
+        worst["x%d" % sp] = float(np.max(np.abs(pg["x"] - po["x"])) / g.dx)
+        assert np.array_equal(pg["flag"], po["flag"])
+    for comp in range(8):
+        worst["f%d" % comp] = float(rel_l2(g.field(comp), o.field(comp)))
+    assert worst["p0"] <= 2e-4 and worst["p1"] <= 2e-4, worst
+    assert worst["x0"] <= 2e-5 and worst["x1"] <= 2e-5, worst
+    assert max(worst["f%d" % c] for c in range(8)) <= 1e-4, worst
+
+
+def test_set_rr_switches_the_kick(picrr):
+    def run(rr_create, switch_to=None):
+        g = picrr.Sim(length_lambda=3, cells_per_lambda=200, rr_on=rr_create, seed=7, sort_interval=8)
+        g.load_foil(0.2, 0.5, 64.0, 1, 1.0, 16)
+        g.inject_laser(300.0, picrr.LP, picrr.ENV_SIN2, 3.0)
+        if switch_to is not None:
+            g.set_rr(switch_to)
+        return g
+
+    # switched off before the first step = created without RR, bit for bit
+    a, b = run(True, 0), run(False)
+    a.step(300)
+    b.step(300)
+    for sp in (0, 1):
+        pa, pb = a.particles(sp), b.particles(sp)
+        for k in ("x", "px", "py", "pz"):
+            assert np.array_equal(pa[k], pb[k]), (sp, k)
+    assert a.energy()[3] == 0.0
+    # mid-run: the radiated tally freezes while the kick is off and grows again after
+    c = run(True)
+    c.step(300)
+    r0 = c.energy()[3]
+    assert r0 > 0.0
+    c.set_rr(0)
+    c.step(50)
+    assert c.energy()[3] == r0
+    c.set_rr(1)
+    c.step(50)
+    assert c.energy()[3] > r0
+    with pytest.raises(picrr.PicError) as e:
+        c.set_rr(2)
+    assert e.value.status == -1
