@@ -40,15 +40,70 @@ UNIT = "particle-steps/s"
 LARGE = dict(length_lambda=100.0, cells_per_lambda=2000.0, cfl=0.95, lambda_um=0.8, rr_on=True,
              source_node=8, foil_x0=0.25, foil_thickness=2.0, ne=100.0, ppc=8000, a0=500.0, pol=1,
              duration=20.0, seed=4, sort_interval=8)
+RUN_STEPS = 2000  # length of the large run
+# step at which the pulse front reaches the foil: (foil front - source node) / cfl
+PULSE_AT_FOIL_STEP = int(math.ceil((LARGE["foil_x0"] * LARGE["cells_per_lambda"] - LARGE["source_node"])
+                                   / LARGE["cfl"]))
 BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int32 + 4 x fp32)
 # DRAM traffic of one push launch of this workload, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum, one launch, 64M particles) for
-# the launch shapes the tuner picks for it, keyed by (particles, particles per
-# unit, sort interval, particles per thread); reported when the run matches
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, 64M particles)
+# with the pulse in the foil, keyed by (particles, particles per unit, sort
+# interval, particles per thread, timed window's first step rounded down to
+# 100, digest of the push kernel's source); a run that does not match every
+# key, or a kernel changed since the capture, reports null
 PUSH_TRAFFIC = {
-    (64_000_000, 16384, 64, 4): 1_280_280_320 + 1_218_965_248,
-    (64_000_000, 16384, 32, 4): 1_280_300_032 + 1_218_996_992,
 }
+
+
+def push_kernel_digest():
+    """First 12 hex digits of the SHA-256 of the push kernel's source file."""
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1008_1685_gb300", "csrc", "k_push.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+
+
+def hot_fractions(sim, w):
+    """Fractions of electrons and ions with kinetic energy above 1 keV (a
+    one-bin spectrum through pic_spectra; counts are sum(w dx) / bin width)."""
+    import numpy as np
+
+    out = {}
+    for sp, name in ((0, "electrons"), (1, "ions")):
+        lo, hi = 1e-3, 1e7
+        c, _ = sim.spectra(sp, 1, lo, hi)
+        wdx = (w["ne"] / w["ppc"]) * (2 * math.pi / w["cells_per_lambda"])
+        n_sp = w["ppc"] * int(round(w["foil_thickness"] * w["cells_per_lambda"]))
+        out[name + "_above_1keV"] = float(np.sum(c) * (hi - lo) / wdx / n_sp)
+    return out
+
+
+def rr_cost_leg(sim, interval, reps=3):
+    """The radiation-reaction kick's cost on one state: whole sort intervals
+    stepped alternately with the kick on and off (pic_set_rr), the push
+    kernel's mean launch time and the whole step's time per rr setting."""
+    per = {1: [], 0: []}
+    step_ms = {1: [], 0: []}
+    k = sim.stats()["steps_since_sort"]
+    if k:
+        sim.step(interval - k)  # to a sort boundary: whole intervals follow, as graph launches
+    for _ in range(reps):
+        for rr in (1, 0):
+            sim.set_rr(rr)
+            sim.set_timing(True)
+            sim.step(interval)
+            st = sim.stats()
+            per[rr].append(st["push_ms"] / max(1, st["timed_push_launches"]))
+            step_ms[rr].append((st["push_ms"] + st["field_ms"] + st["sort_ms"]) / interval)
+    sim.set_rr(1)
+    on, off = statistics.median(per[1]), statistics.median(per[0])
+    son, soff = statistics.median(step_ms[1]), statistics.median(step_ms[0])
+    return {"push_ms_rr_on": on, "push_ms_rr_off": off, "push_ratio": on / off,
+            "step_ms_rr_on": son, "step_ms_rr_off": soff, "step_ratio": son / soff,
+            "paper": "about +10 % computing time with the RR force (Sec. 3, last paragraph)",
+            "how": "%d alternating pairs of %d-step intervals on the same run after the timed window; "
+                   "medians; push = the fused kernel's mean launch time, step = push + Yee + sort per step"
+                   % (reps, interval)}
 
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
@@ -326,23 +381,98 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(steps, ppc=50):
-    """The FP64 oracle on the large run's grid and foil with ppc per species."""
+def oracle_sample(steps, ppc=400, parallel=True):
+    """The FP64 oracle on the large run's grid and foil with ppc per species,
+    the first `steps` steps (the oracle's cost per particle does not depend on
+    the state: it has no sort and skips nothing but frozen particles).
+    parallel: the OpenMP timing build on all host cores (OMP_NUM_THREADS)."""
     import oracle
 
+    par = parallel and oracle.parallel_available()
     w = LARGE
     o = oracle.OracleSim(w["length_lambda"], w["cells_per_lambda"], w["cfl"], w["lambda_um"], w["rr_on"],
-                         w["source_node"])
+                         w["source_node"], parallel=par)
     o.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, ppc, w["seed"])
     o.inject_laser(w["a0"], w["pol"], 0, w["duration"])
-    n_part = 2 * len(o.particles(0)["x"])
+    n_part = 2 * ppc * int(round(w["foil_thickness"] * w["cells_per_lambda"]))
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     o.close()
+    cores = oracle.threads() if par else 1
     sample = ("large-run grid (200,000 cells) and foil with %d macro-particles per cell per species "
-              "(%d particles), first %d steps, FP64, one thread" % (ppc, n_part, steps))
-    return n_part * steps / dt, sample
+              "(%d particles), first %d steps, FP64, %d threads" % (ppc, n_part, steps, cores))
+    return n_part * steps / dt, sample, cores
+
+
+# the small single run (20 lambda at lambda/200, 1-lambda foil at 10 lambda, n_e = 64 n_c, 64 ppc per
+# species, LP a0 = 200, 10-period sin^2 pulse, RR on, 4211 steps) and the paper-scale run (60 lambda at
+# lambda/1000, 1-lambda foil at 10 lambda, n_e = 90 n_c, 400 ppc, a0 = 350 LP, 20-period pulse)
+SMALL = dict(length_lambda=20.0, cells_per_lambda=200.0, foil_x0=10.0, foil_thickness=1.0, ne=64.0, ppc=64,
+             a0=200.0, pol=0, duration=10.0, steps=4211, seed=1)
+PAPER = dict(length_lambda=60.0, cells_per_lambda=1000.0, foil_x0=10.0, foil_thickness=1.0, ne=90.0, ppc=400,
+             a0=350.0, pol=0, duration=20.0, steps=500, seed=11)
+
+
+def _oracle_run(d, steps, parallel):
+    import oracle
+
+    o = oracle.OracleSim(d["length_lambda"], d["cells_per_lambda"], 0.95, 0.8, True, 8, parallel=parallel)
+    o.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"], d["seed"])
+    o.inject_laser(d["a0"], d["pol"], 0, d["duration"])
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    n = 2 * d["ppc"] * int(round(d["foil_thickness"] * d["cells_per_lambda"]))
+    o.close()
+    return el, n
+
+
+def _oracle_scan_worker(args):
+    i, steps = args
+    d = scan_desc(i)
+    run = dict(length_lambda=d["length_lambda"], cells_per_lambda=SCAN["cells_per_lambda"], foil_x0=d["foil_x0"],
+               foil_thickness=d["foil_thickness"], ne=d["ne"], ppc=d["ppc"], a0=d["a0"], pol=d["polarization"],
+               duration=d["duration"], seed=d["seed"])
+    el, n = _oracle_run(run, steps, False)
+    return el, n, d["steps"]
+
+
+def cpu_plan_leg(scan_runs=16, scan_steps=800):
+    """The oracle on the host cores for the workloads the GPU legs run: the
+    small single run in full and the paper-scale run's first 500 steps (the
+    OpenMP build, all cores), and 16 scan runs in 16 processes (the serial
+    build, one run each) for their first scan_steps steps, extrapolated to
+    the full run length and to the 256-run scan."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import oracle
+
+    par = oracle.parallel_available()
+    out = {"threads": oracle.threads() if par else 1, "nproc": os.cpu_count()}
+    el, n = _oracle_run(SMALL, SMALL["steps"], par)
+    out["small_run_full"] = {"seconds": el, "particle_steps_per_s": n * SMALL["steps"] / el,
+                             "runs_per_hour": 3600.0 / el,
+                             "what": "20 lambda at lambda/200, 12,800 + 12,800 particles, LP a0 = 200, all 4211 steps"}
+    el, n = _oracle_run(PAPER, PAPER["steps"], par)
+    out["paper_scale_500_steps"] = {"seconds": el, "particle_steps_per_s": n * PAPER["steps"] / el,
+                                    "what": "60,000 cells, 400k + 400k particles, first 500 steps"}
+    workers = min(scan_runs, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_scan_worker, [(i, scan_steps) for i in range(scan_runs)]))
+    wall = time.perf_counter() - t0
+    full = sum(el * total / scan_steps for el, _, total in res)  # one core, all 16 runs in full
+    ps = sum(n * scan_steps for _, n, _ in res)
+    out["batched_scan"] = {
+        "runs_timed": scan_runs, "steps_timed": scan_steps, "processes": workers, "wall_s": wall,
+        "particle_steps_per_s": ps / wall,
+        "runs_per_hour_extrapolated": 3600.0 * scan_runs / (full / workers),
+        "what": "the scan's first %d runs, one process each (serial oracle), first %d of their 21,053 steps; "
+                "runs/h extrapolated to full length and to %d processes running the 256 runs"
+                % (scan_runs, scan_steps, workers)}
+    return out
 
 
 def run_reference(args):
@@ -350,17 +480,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     vals = []
-    for _ in range(args.warmup):
-        oracle_sample(2)
+    oracle_sample(2, ppc=args.ref_ppc)
     for _ in range(max(1, args.steps)):
-        v, sample = oracle_sample(args.ref_steps)
+        v, sample, cores = oracle_sample(args.ref_steps, ppc=args.ref_ppc)
         vals.append(v)
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": large_workload(), "cells": 200000},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -434,10 +563,13 @@ def e2e_run(picrr, torch, device, steps, host, shapes=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=384)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--ref-steps", type=int, default=40)
+    ap.add_argument("--ref-steps", type=int, default=40, help="steps of each oracle sample")
+    ap.add_argument("--ref-ppc", type=int, default=400, help="particles per cell per species of the oracle sample")
+    ap.add_argument("--no-cpu-plan", action="store_true",
+                    help="skip the oracle timings of the small run, the paper-scale run and the scan")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no tuner run)")
@@ -458,6 +590,10 @@ def main():
                     help="admission order of both serving arms: least work first, or arrival order")
     ap.add_argument("--serve-resident", type=int, default=SERVE["resident"],
                     help="particles stepping at once in the server (0: no cap)")
+    ap.add_argument("--preroll", type=int, default=PULSE_AT_FOIL_STEP + 82,
+                    help="untimed steps before the tuner; the timed window ends at step 2000 when it fits after "
+                         "them")
+    ap.add_argument("--no-rr-cost", action="store_true", help="skip the RR on/off timing after the window")
     ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
                     help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
@@ -487,26 +623,38 @@ def main():
         v = [int(x) for x in args.shapes.split(",")]
         shapes = {"unit_particles": v[0], "sort_interval": v[1], "particles_per_thread": v[2] if len(v) > 2 else 4,
                   "tuned": False}
-    elif not args.no_tune:
-        # launch shapes picked by the tuner on an identical run (its trial steps are
-        # real steps, so the measured run starts fresh)
-        t = make_sim(picrr, local)
-        t.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
-        t.inject_laser(w["a0"], w["pol"], 0, w["duration"])
-        unit, interval, ppt, tms = t.tune_shapes(64)
-        t.close()
-        shapes = {"unit_particles": unit, "sort_interval": interval, "particles_per_thread": ppt, "tuned": True,
-                  "trial_ms_per_step": {"particles_per_thread_4_2": [round(v, 4) for v in tms[:2]],
-                                        "unit_2048_4096_8192_16384": [round(v, 4) for v in tms[2:6]],
-                                        "interval_8_16_32_64": [round(v, 4) for v in tms[6:]]}}
-    sim = make_sim(picrr, local)
+    sim = make_sim(picrr, local, w)
     sim.load_foil(w["foil_x0"], w["foil_thickness"], w["ne"], 1, 1.0, w["ppc"])
     sim.inject_laser(w["a0"], w["pol"], 0, w["duration"])
     if shapes:
         sim.set_shapes(shapes["unit_particles"], shapes["sort_interval"], shapes["particles_per_thread"])
     stream = torch.cuda.current_stream()
     sim.set_stream(stream.cuda_stream)
+    # untimed pre-roll: the pulse front reaches the foil at step ~518; the
+    # tuner (whose trial steps are real steps of this run) and the timed
+    # window both run with the pulse in the foil
+    sim.step(args.preroll)
+    if shapes is None and not args.no_tune:
+        unit, interval, ppt, tms = sim.tune_shapes(64)
+        shapes = {"unit_particles": unit, "sort_interval": interval, "particles_per_thread": ppt, "tuned": True,
+                  "tuned_from_step": sim.stats()["steps"],
+                  "trial_ms_per_step": {"particles_per_thread_4_2": [round(v, 4) for v in tms[:2]],
+                                        "unit_2048_4096_8192_16384": [round(v, 4) for v in tms[2:6]],
+                                        "interval_8_16_32_64": [round(v, 4) for v in tms[6:]]}}
+    interval = shapes["sort_interval"] if shapes else w["sort_interval"]
+    # the timed window ends at the run's last step (2000) when it fits after
+    # the pre-roll, the tuner, one sort interval timed for the amortised sort
+    # cost and the warm-up; otherwise it starts right after them
+    now = sim.stats()["steps"]
+    start = max(RUN_STEPS - args.steps, now + 2 * interval + args.warmup)
+    sim.step(start - args.warmup - 2 * interval - now)
+    sim.set_timing(True)
+    sa = sim.stats()
+    sim.step(2 * interval)  # holds at least one whole sort (timed on the launching stream)
+    sb = sim.stats()
+    sort_ms_mean = sb["sort_ms"] / max(1, sb["sort_count"] - sa["sort_count"])
     sim.step(args.warmup)
+    hot = hot_fractions(sim, w)
     st0 = sim.stats()
     n_active = st0["active_particles"]
 
@@ -517,7 +665,7 @@ def main():
     clocks = Clocks(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
-    sim.set_timing(True)
+    sim.set_timing(True)  # counters cover the timed window only
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if clocks:
         clocks.begin()
@@ -528,10 +676,15 @@ def main():
     if clocks:
         clocks.end()
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms_raw = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None
     st1 = sim.stats()
     n_active_end = st1["active_particles"]
+    # whatever sorts fell inside the K timed steps are replaced by K / interval
+    # sorts of the mean measured duration, so that the value holds the
+    # amortised sort at any K
+    sorts_in = st1["sort_count"] - st0["sort_count"]
+    ms = ms_raw - st1["sort_ms"] + args.steps * sort_ms_mean / interval
     ms_max, total = aggregate(torch, dist, ms, float(n_active) * args.steps)
     value = total / (ms_max / 1e3)
     push_avg_ms = st1["push_ms"] / max(1, st1["timed_push_launches"])
@@ -541,18 +694,24 @@ def main():
     traffic = None
     if shapes:
         traffic = PUSH_TRAFFIC.get((n_active, shapes["unit_particles"], shapes["sort_interval"],
-                                    shapes["particles_per_thread"]))
+                                    shapes["particles_per_thread"], start // 100 * 100, push_kernel_digest()))
+    window = {"first_step": start, "last_step": start + args.steps - 1, "ms_raw": ms_raw, "sorts_inside": sorts_in,
+              "sort_ms_inside": st1["sort_ms"], "sort_ms_mean": sort_ms_mean, "sort_interval": interval,
+              "ms_with_amortised_sort": ms, "kernel_launches_before": st0["kernel_launches"],
+              "push_launches_before": st0["push_launches"]}
+    rr_cost = None if args.no_rr_cost else rr_cost_leg(sim, interval)
     sim.close()
 
     e2e = None
     if not args.no_e2e:
         host = host_foil(np, torch)
-        ev, h2d, d2h = e2e_run(picrr, torch, local, args.steps, host, shapes)
-        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-               "d2h_bytes_per_step": d2h / args.steps,
+        n_e2e = start + args.steps
+        ev, h2d, d2h = e2e_run(picrr, torch, local, n_e2e, host, shapes)
+        e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e,
+               "d2h_bytes_per_step": d2h / n_e2e, "steps": n_e2e,
                "what": "pic_create + pic_load_particles_f32 from pinned host SoA + pic_inject_laser + "
-                       "pic_set_shapes (the tuned shapes) + pic_step_n(steps) + pic_spectra + pic_energy, "
-                       "host wall clock"}
+                       "pic_set_shapes (the tuned shapes) + pic_step_n(steps 0 .. end of the timed window) + "
+                       "pic_spectra + pic_energy, host wall clock"}
 
     scan = None
     if args.scan_runs > 0:
@@ -596,18 +755,22 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, sample = oracle_sample(args.ref_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        v, sample, cores = oracle_sample(args.ref_steps, ppc=args.ref_ppc)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if not args.no_cpu_plan:
+            cpu["plan"] = cpu_plan_leg()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": large_workload(args.ppc),
+            "config": {"workload": large_workload(args.ppc) + "; timed steps %d..%d of the 2000-step run (the "
+                                   "pulse front reaches the foil at step %d)"
+                                   % (start, start + args.steps - 1, PULSE_AT_FOIL_STEP),
                        "particles": n_active, "particles_end": n_active_end, "cells": 200000,
-                       "sort_interval": shapes["sort_interval"] if shapes else w["sort_interval"],
-                       "shapes": shapes,
+                       "sort_interval": interval,
+                       "shapes": shapes, "hot_at_window_start": hot,
                        "l2": "inputs larger than L2: 2.56 GB particle state streamed per step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -616,7 +779,9 @@ def main():
                          "peak_kind": peak_kind,
                          "bytes_per_launch": BYTES_PER_PARTICLE_STEP * n_active},
             "step_breakdown_ms": {"push": st1["push_ms"] / args.steps, "field": st1["field_ms"] / args.steps,
-                                  "sort": st1["sort_ms"] / args.steps},
+                                  "sort_amortised": sort_ms_mean / interval},
+            "timed_window": window,
+            "rr_cost": rr_cost,
             "runs_per_hour": 3600.0 / (2000 * ms_max / args.steps / 1e3) * ws,
             "batched_scan": scan,
             "serving": serving,

@@ -7,7 +7,9 @@ It shares no code with the CUDA library and the CUDA library never calls it.
 
 The arithmetic lives in ``pic_oracle.c`` (plain C, IEEE double, no FMA
 contraction); this module only loads the shared object and marshals
-arguments.  ``planewave.py`` holds the closed-form plane-wave solutions used
+arguments.  ``pic_oracle_omp.c`` builds the same code a second time with the
+particle loop split over OpenMP threads: a timing build for the CPU baseline,
+checked against the serial build, never the checker itself.  ``planewave.py`` holds the closed-form plane-wave solutions used
 to pin the pusher.
 """
 from __future__ import annotations
@@ -21,6 +23,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "pic_oracle.c")
+# the parallel timing build (OpenMP over the particles of each species)
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_SRC_OMP = os.path.join(_HERE, "pic_oracle_omp.c")
 
 LP, CP = 0, 1
 ENV_SIN2, ENV_TRAPEZOID = 0, 1
@@ -33,18 +38,30 @@ def ecr(lambda_um):
     return lib().or_ecr(lambda_um)
 
 
+def _stale(so, srcs):
+    return not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(f) for f in srcs)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (ISO C11, -O2, no FP contraction)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
-    ):
+    """Compile the oracle with gcc (ISO C11, -O2, no FP contraction), and its
+    parallel timing build with -fopenmp where the compiler supports it."""
+    hdr = os.path.join(_HERE, "oracle.h")
+    flags = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    if force or _stale(_SO, [_SRC, hdr]):
         tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"]
-        )
+        subprocess.check_call(["gcc", *flags, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
+    if force or _stale(_SO_OMP, [_SRC, _SRC_OMP, hdr]):
+        tmp = _SO_OMP + ".tmp%d" % os.getpid()
+        r = subprocess.run(["gcc", *flags, "-fopenmp", "-o", tmp, _SRC_OMP, "-lm"], capture_output=True)
+        if r.returncode == 0:
+            os.replace(tmp, _SO_OMP)
     return _SO
+
+
+def parallel_available() -> bool:
+    build()
+    return os.path.exists(_SO_OMP)
 
 
 class _Config(C.Structure):
@@ -58,14 +75,18 @@ class _Config(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(parallel: bool = False):
+    """The oracle's shared object; parallel=True: the OpenMP timing build."""
+    if parallel not in _libs:
         build()
-        L = C.CDLL(_SO)
+        if parallel and not os.path.exists(_SO_OMP):
+            raise RuntimeError("the parallel oracle build needs a C compiler with OpenMP")
+        L = C.CDLL(_SO_OMP if parallel else _SO)
+        if parallel:
+            L.or_threads.restype = C.c_int
         dp = C.POINTER(C.c_double)
         L.or_eps_rr.restype = C.c_double
         L.or_eps_rr.argtypes = [C.c_double]
@@ -104,8 +125,13 @@ def lib():
         L.or_ecr.argtypes = [C.c_double]
         L.or_read_fields.restype = C.c_int64
         L.or_read_fields.argtypes = [C.c_void_p, C.c_int, C.c_int64, dp]
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads() -> int:
+    """OpenMP threads the parallel build uses (OMP_NUM_THREADS, else all cores)."""
+    return lib(True).or_threads()
 
 
 def _dp(a):
@@ -156,9 +182,9 @@ class OracleSim:
     """The FP64 1D PIC with the same call sequence as the CUDA library."""
 
     def __init__(self, length_lambda, cells_per_lambda, cfl=0.95, lambda_um=0.8, rr_on=True,
-                 source_node=8):
+                 source_node=8, parallel=False):
         cfg = _Config(length_lambda, cells_per_lambda, cfl, lambda_um, int(rr_on), source_node)
-        self._L = lib()
+        self._L = lib(parallel)
         self._h = self._L.or_create(C.byref(cfg))
         if not self._h:
             raise ValueError("oracle: invalid configuration")

@@ -470,11 +470,12 @@ static void deposit(or_sim* s, double a, double xi0, double xi1, double vy, doub
     }
 }
 
-static void push_species(or_sim* s, int k) {
+/* Push and deposit particles i0 .. i1-1 of species k, in index order. */
+static void push_range(or_sim* s, int k, int64_t i0, int64_t i1) {
     or_species* sp = &s->sp[k];
     double qm = sp->q / sp->m, a = sp->q * sp->w;
     int rr = (k == 0 && s->rr_on);
-    for (int64_t i = 0; i < sp->n; i++) {
+    for (int64_t i = i0; i < i1; i++) {
         if (sp->flag[i]) continue; /* frozen at a wall */
         double E[3], B[3], p[3] = {sp->px[i], sp->py[i], sp->pz[i]};
         double xi = sp->xi[i];
@@ -499,6 +500,12 @@ static void push_species(or_sim* s, int k) {
         sp->pz[i] = p[2];
     }
 }
+
+static void push_species(or_sim* s, int k) { push_range(s, k, 0, s->sp[k].n); }
+
+#ifdef OR_PARALLEL_PUSH
+static void push_species_parallel(or_sim* s, int k); /* pic_oracle_omp.c */
+#endif
 
 /* B half advance, B -= (dt/2) curl E, with the TF/SF correction at the last
  * scattered-field half node for the incident E at time t. */
@@ -556,8 +563,14 @@ int or_step_n(or_sim* s, int64_t n) {
         memset(s->Jx - OR_PAD, 0, len * sizeof(double));
         memset(s->Jy - OR_PAD, 0, len * sizeof(double));
         memset(s->Jz - OR_PAD, 0, len * sizeof(double));
-        for (int k = 0; k < 2; k++)
-            if (s->sp[k].loaded) push_species(s, k);
+        for (int k = 0; k < 2; k++) {
+            if (!s->sp[k].loaded) continue;
+#ifdef OR_PARALLEL_PUSH
+            push_species_parallel(s, k);
+#else
+            push_species(s, k);
+#endif
+        }
         field_step(s);
         s->step++;
     }
