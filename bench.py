@@ -175,12 +175,22 @@ def _latency_summary(lat, pending_ages, elapsed, n_req):
             "runs_per_hour": 3600.0 * len(lat) / elapsed}
 
 
-def serve_leg(picrr, device, cfg=SERVE, w=SCAN):
+def my_requests(picrr, cfg, w, rank, ws):
+    """This rank's share of the request stream: each request goes, in arrival
+    order, to the rank with the least work so far (pic_shard_runs)."""
+    reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    if ws == 1 or not reqs:
+        return reqs
+    ranks, _ = shard(picrr, [d for _, d in reqs], ws, in_order=True, w=w)
+    return [q for q, r in zip(reqs, ranks) if r == rank]
+
+
+def serve_leg(picrr, device, cfg=SERVE, w=SCAN, rank=0, ws=1):
     """Continuous batching through pic_server: requests are submitted at their
     arrival times; latency = submission to spectra on the host."""
     import threading
 
-    reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    reqs = my_requests(picrr, cfg, w, rank, ws)
     srv = picrr.Server(w["cells_per_lambda"], max_runs=cfg["max_runs"], chunk_steps=cfg["chunk"], cfl=w["cfl"],
                        sort_interval=w["sort_interval"], device=device, hbm_budget_bytes=cfg["budget"])
     srv.set_policy(picrr.SERVE_SHORTEST_FIRST if cfg["policy"] == "sjf" else picrr.SERVE_FIFO, cfg["resident"])
@@ -220,11 +230,11 @@ def serve_leg(picrr, device, cfg=SERVE, w=SCAN):
     return out
 
 
-def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
+def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN, rank=0, ws=1):
     """The same request stream served one run at a time through the
     single-run API (no batching), under the same time cap and the same order
     policy (arrival order, or the least work among the arrived requests)."""
-    reqs = serve_requests(cfg["rate"], cfg["window_s"], cfg["seed"], w)
+    reqs = my_requests(picrr, cfg, w, rank, ws)
     work = [desc_particles(d, w["cells_per_lambda"]) * d["steps"] for _, d in reqs]
     t0 = time.perf_counter()
     lat, pending = [], list(range(len(reqs)))
@@ -254,12 +264,22 @@ def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN):
     return _latency_summary(lat, [el - reqs[j][0] for j in pending if reqs[j][0] <= el], el, len(reqs))
 
 
-def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None, first=0):
-    """All runs in one batch (one launch per kernel per step for all of them),
-    from creation to every run's ion spectrum on the host.  max_steps (for
-    profiling) cuts every run short; first: index of the first run (each rank
-    of a multi-GPU job takes its own runs)."""
-    descs = [scan_desc(first + i, w) for i in range(n_runs)]
+def shard(picrr, descs, ranks, in_order=False, w=SCAN):
+    """The rank of each run description (pic_shard_runs: least-work rank
+    first, largest runs first unless in_order); every rank computes the same."""
+    rd = [picrr.run_desc(d["length_lambda"], d["foil_x0"], d["foil_thickness"], d["ne"], d["a0"],
+                         d["polarization"], d["duration"], d["steps"], rr_on=d["rr_on"], ppc=d["ppc"], seed=d["seed"])
+          for d in descs]
+    return picrr.shard_runs(rd, ranks, w["cells_per_lambda"], in_order=in_order)
+
+
+def batched_scan(picrr, device, run_ids, w=SCAN, max_steps=None):
+    """The scan runs run_ids (indices into the scan's seed sequence) in one
+    batch (one launch per kernel per step for all of them), from creation to
+    every run's ion spectrum on the host.  max_steps (for profiling) cuts
+    every run short."""
+    n_runs = len(run_ids)
+    descs = [scan_desc(i, w) for i in run_ids]
     if max_steps:
         descs = [dict(d, steps=min(d["steps"], max_steps)) for d in descs]
     t0 = time.perf_counter()
@@ -280,10 +300,11 @@ def batched_scan(picrr, device, n_runs, w=SCAN, max_steps=None, first=0):
                 push_launches=st["push_launches"], kernel_launches=st["kernel_launches"])
 
 
-def plain_scan(picrr, device, n_runs, w=SCAN, first=0):
+def plain_scan(picrr, device, run_ids, w=SCAN):
     """The same runs one at a time through the single-run API (create, foil,
     laser, step to the end, ion spectrum, destroy), on the same GPU."""
-    descs = [scan_desc(first + i, w) for i in range(n_runs)]
+    n_runs = len(run_ids)
+    descs = [scan_desc(i, w) for i in run_ids]
     t0 = time.perf_counter()
     for d in descs:
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
@@ -296,6 +317,89 @@ def plain_scan(picrr, device, n_runs, w=SCAN, first=0):
     el = time.perf_counter() - t0
     ps = sum(desc_particles(d, w["cells_per_lambda"]) * d["steps"] for d in descs)
     return dict(runs=n_runs, seconds=el, runs_per_hour=3600.0 * n_runs / el, particle_steps_per_s=ps / el)
+
+
+def parity_leg(picrr, device):
+    """The GPU's errors against the FP64 oracle on small seeded cases, outside
+    any timed region: the oracle's results are stored in
+    tests/golden/oracle_parity_cases.json and oracle_small_run_ensemble.json
+    (written by scripts there that call only the oracle); the inputs are
+    regenerated from the same seeds by tests/synth.py."""
+    import numpy as np
+
+    from tests import synth
+    from tests.spectrum_stats import balance, peak_fwhm
+
+    gold = os.path.join(ROOT, "tests", "golden")
+    G = json.load(open(os.path.join(gold, "oracle_parity_cases.json")))
+    out = {}
+    c = G["one_step"]
+    g = picrr.Sim(seed=1, sort_interval=8, device=device, **c["box"])
+    F = synth.random_fields(g.nx, **c["fields"])
+    g.set_fields(*F)
+    for sp, s in enumerate(c["species"]):
+        p = synth.random_particles(s["n"], 2, g.nx - 2, s["pscale"], s["seed"])
+        g.load_particles(sp, *p, s["weight"], s["charge"], s["mass"])
+    g.step(1)
+    worst_p, worst_x = 0.0, 0.0
+    for sp in (0, 1):
+        q, r = g.particles(sp), c["result"][sp]
+        pg = np.stack([q["px"], q["py"], q["pz"]], 1)
+        po = np.stack([np.array(r["px"]), np.array(r["py"]), np.array(r["pz"])], 1)
+        scale = np.maximum(np.linalg.norm(po, axis=1), 1e-3 * c["fields"]["scale"] * g.dt)
+        worst_p = max(worst_p, float(np.max(np.max(np.abs(pg - po), axis=1) / scale)))
+        worst_x = max(worst_x, float(np.max(np.abs(q["x"] - np.array(r["x"]))) / g.dx))
+    g.close()
+    out["momentum_1_step"] = {"max_rel": worst_p, "tolerance": 1e-5,
+                              "what": "per particle max-norm difference / max(|p|, 1e-3 F dt), 1000 e + 500 p"}
+    out["position_1_step"] = {"max_cells": worst_x}
+    c = G["fields_200"]
+    g = picrr.Sim(seed=c["foil"]["seed"], sort_interval=8, device=device, **c["box"])
+    f, la = c["foil"], c["laser"]
+    g.load_foil(f["x0"], f["thickness"], f["ne"], f["Z"], f["A"], f["ppc"])
+    g.inject_laser(la["a0"], la["polarization"], la["envelope"], la["duration"])
+    g.step(c["steps"])
+    groups = {"E_perp": (1, 2), "B_perp": (3, 4), "Ex": (0,)}
+    l2 = {}
+    for name, comps in groups.items():
+        a = np.concatenate([g.field(k) for k in comps])
+        b = np.concatenate([np.array(c["result"][k]) for k in comps])
+        l2[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    g.close()
+    out["fields_200_steps"] = {"rel_l2": l2, "tolerance": 1e-4}
+    c = G["balance"]
+    g = picrr.Sim(seed=c["foil"]["seed"], sort_interval=8, device=device, **c["box"])
+    f, la = c["foil"], c["laser"]
+    g.load_foil(f["x0"], f["thickness"], f["ne"], f["Z"], f["A"], f["ppc"])
+    g.inject_laser(la["a0"], la["polarization"], la["envelope"], la["duration"])
+    b, e = balance(g, c["steps"], c["every"])
+    g.close()
+    out["energy_balance"] = {"gpu_max_over_injected": float(np.max(np.abs(b)) / e[4]),
+                             "oracle_max_over_injected": c["result"]["max_abs_over_injected"],
+                             "tolerance": 1e-3, "what": "small single run, 4211 steps, time-centred balance"}
+    E = json.load(open(os.path.join(gold, "oracle_small_run_ensemble.json")))
+    seeds = E["seeds"]
+    nb, e_max = E["bins"]["n"], E["bins"]["e_max"]
+    bt = picrr.Batch(E["small"]["cells_per_lambda"], max_runs=len(seeds), sort_interval=8, device=device)
+    f, la = E["foil"], E["laser"]
+    ids = [bt.add_run(E["small"]["length_lambda"], f["x0"], f["thickness"], f["ne"], la["a0"], la["polarization"],
+                      la["duration"], E["steps"], rr_on=True, ppc=f["ppc"], seed=sd) for sd in seeds]
+    while bt.step(4096) > 0:
+        pass
+    spec_g = sum(bt.spectra(r, 1, nb, 0.0, e_max)[0] for r in ids)
+    rad_g = float(np.mean([bt.energy(r)[3] for r in ids]))
+    bt.close()
+    spec_o = np.array(E["spectrum_sum"])
+    pg, fg = peak_fwhm(spec_g, 0.0, e_max)
+    po, fo = peak_fwhm(spec_o, 0.0, e_max)
+    ec = (np.arange(nb) + 0.5) * e_max / nb
+    mg, mo = float(spec_g @ ec / spec_g.sum()), float(spec_o @ ec / spec_o.sum())
+    rad_o = float(np.mean(E["radiated"]))
+    out["ensemble_%d_seeds" % len(seeds)] = {
+        "peak_rel": pg / po - 1.0, "fwhm_rel": fg / fo - 1.0, "mean_energy_rel": mg / mo - 1.0,
+        "radiated_rel": rad_g / rad_o - 1.0, "tolerance": 0.02,
+        "what": "ion spectra of the small single run summed over foil seeds (full runs are chaotic)"}
+    return out
 
 
 def _dist():
@@ -594,6 +698,7 @@ def main():
                     help="untimed steps before the tuner; the timed window ends at step 2000 when it fits after "
                          "them")
     ap.add_argument("--no-rr-cost", action="store_true", help="skip the RR on/off timing after the window")
+    ap.add_argument("--no-parity", action="store_true", help="skip the errors against the stored oracle results")
     ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
                     help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
@@ -715,24 +820,34 @@ def main():
 
     scan = None
     if args.scan_runs > 0:
-        # weak scaling: rank r takes runs [r * n, (r + 1) * n) of the scan's seed sequence
-        scan = batched_scan(picrr, local, args.scan_runs, max_steps=args.scan_steps or None,
-                            first=rank * args.scan_runs)
+        # the scan's runs split over the ranks by work (strong scaling: the
+        # whole job steps the same runs at any N)
+        ranks, loads = shard(picrr, [scan_desc(i) for i in range(args.scan_runs)], ws)
+        mine = [i for i, r in enumerate(ranks) if r == rank]
+        scan = batched_scan(picrr, local, mine, max_steps=args.scan_steps or None)
         if args.plain_runs > 0:
-            plain = plain_scan(picrr, local, min(args.plain_runs, args.scan_runs), first=rank * args.scan_runs)
+            plain = plain_scan(picrr, local, mine[:args.plain_runs])
             scan["plain"] = plain
             scan["speedup_runs_per_hour"] = scan["runs_per_hour"] / plain["runs_per_hour"]
         scan["workload"] = ("%d runs, 15,000 cells (30 lambda, lambda/500), 21,053 steps each; a0 U[100,600], "
                             "thickness U[0.5,2] lambda, n_e U[30,150] n_c, LP/CP, RR on/off, ppc U{32..256}; "
                             "plain = the first %d of the same runs one at a time" % (args.scan_runs, args.plain_runs))
         ms_scan, _ = aggregate(torch, dist, scan["seconds"] * 1e3, 0.0)
-        scan["runs_per_hour"] = 3600.0 * args.scan_runs * ws / (ms_scan / 1e3)
+        scan["runs_per_hour"] = 3600.0 * args.scan_runs / (ms_scan / 1e3)
+        scan["scaling"] = "strong"
+        scan["sharding"] = {"ranks": ws, "runs_per_rank": [ranks.count(r) for r in range(ws)],
+                            "particle_steps_per_rank": [float(x) for x in loads]}
 
     serving = None
     if args.serve_window > 0:
         def one_stream(cfg):
-            out = serve_leg(picrr, local, cfg)
-            out["plain"] = plain_serve_leg(picrr, local, cfg)
+            out = serve_leg(picrr, local, cfg, rank=rank, ws=ws)
+            out["plain"] = plain_serve_leg(picrr, local, cfg, rank=rank, ws=ws)
+            if ws > 1:
+                ms_all, done_all = aggregate(torch, dist, out["elapsed_s"] * 1e3, float(out["completed"]))
+                out["share"] = "rank 0's share of the stream (requests split over %d ranks as they arrive)" % ws
+                out["completed_all_ranks"] = int(done_all)
+                out["runs_per_hour_all_ranks"] = 3600.0 * done_all / (ms_all / 1e3)
             out["overloaded"] = out["unfinished"] > 0  # the queue had not drained when the cap ended the arm
             out["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
                                "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
@@ -744,14 +859,18 @@ def main():
                                   cfg["cap_s"]))
             return out
 
-        # each rank of a multi-GPU job serves its own request stream (weak scaling); rank 0 reports its own
+        # one request stream split over the ranks as the requests arrive; rank 0 reports its share
         cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
-                   policy=args.serve_policy, resident=args.serve_resident, seed=SERVE["seed"] + 1000 * rank)
+                   policy=args.serve_policy, resident=args.serve_resident)
         serving = one_stream(cfg)
         if args.serve_low_rate > 0:
             low = dict(SERVE_LOW, cap_s=args.serve_cap, rate=args.serve_low_rate, policy=args.serve_policy,
-                       resident=args.serve_resident, seed=SERVE_LOW["seed"] + 1000 * rank)
+                       resident=args.serve_resident)
             serving["sustainable_rate"] = one_stream(low)
+
+    parity = None
+    if rank == 0 and not args.no_parity:
+        parity = parity_leg(picrr, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -789,6 +908,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "parity": parity,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

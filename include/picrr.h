@@ -339,6 +339,24 @@ pic_status pic_batch_release_run(pic_batch* batch, int run);
  * admission by memory.  Reads only the batch's configuration, so it may be
  * called from any thread; its error message is pic_batch_last_error(NULL). */
 pic_status pic_batch_run_footprint(const pic_batch* batch, const pic_run_desc* desc, size_t* bytes);
+
+/* Split independent runs over n_ranks GPUs, one process (rank) per GPU.  The
+ * paper has no counterpart: it is the scheduling of a scan or a request stream
+ * of independent runs.  Host only (no device call).  The work of a run is its
+ * particle-steps (both species: 2 * ppc * cells of the foil * steps); each run
+ * goes to the rank with the least work assigned so far among those whose
+ * assigned footprints (pic_batch_run_footprint for common->cells_per_lambda,
+ * summed, as if all runs of a rank were resident at once) stay within
+ * budget_per_rank bytes (0: no limit); ties go to the lowest rank.
+ * in_order = 0: runs taken in decreasing order of work (a scan known in
+ * advance); in_order = 1: in the given order (a request stream, assigned as
+ * the requests arrive).  The result depends only on the arguments, so every
+ * rank computes the same assignment without exchanging anything.
+ * rank_of_run[n_runs] receives the rank of each run; work_per_rank[n_ranks]
+ * (nullable) the particle-steps assigned to each rank.  PIC_ERR_OOM (nothing
+ * written) if a run fits no rank; errors are reported by pic_last_error(NULL). */
+pic_status pic_shard_runs(const pic_config* common, const pic_run_desc* runs, int n_runs, int n_ranks,
+                          int in_order, size_t budget_per_rank, int* rank_of_run, double* work_per_rank);
 /* As pic_set_shapes / pic_tune_shapes, for all active runs of the batch together. */
 pic_status pic_batch_set_shapes(pic_batch* batch, int unit_particles, int sort_interval, int particles_per_thread);
 pic_status pic_batch_tune_shapes(pic_batch* batch, int64_t steps_per_candidate, int* unit_particles,

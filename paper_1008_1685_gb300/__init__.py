@@ -8,6 +8,6 @@ CPU fallback, and importing the binding raises if the library is missing.
 """
 from .binding import (  # noqa: F401
     BY, BZ, CP, ELECTRON, ENV_SIN2, ENV_TRAPEZOID, EX, EY, EZ, ION, JX, JY, JZ, LP, SERVE_FIFO,
-    SERVE_SHORTEST_FIRST, INTEGRATOR_LEAPFROG, INTEGRATOR_RK4, ElectronCase, electron_scan, selftest_wait_timeout,
+    SERVE_SHORTEST_FIRST, INTEGRATOR_LEAPFROG, INTEGRATOR_RK4, ElectronCase, electron_scan, selftest_wait_timeout, shard_runs,
     Batch, PicError, RunDesc, Server, ServerStats, Sim, Stats, library, library_path, run_desc,
 )

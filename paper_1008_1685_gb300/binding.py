@@ -36,7 +36,7 @@ SYMBOLS = ("pic_create", "pic_set_stream", "pic_load_foil", "pic_load_particles"
            "pic_batch_tune_shapes", "pic_set_shapes", "pic_batch_set_shapes", "pic_server_set_policy",
            "pic_snapshot", "pic_batch_snapshot",
            "pic_electron_scan", "pic_selftest_wait_timeout", "pic_batch_stop_run", "pic_server_cancel",
-           "pic_save", "pic_restore", "pic_get_config", "pic_set_rr")
+           "pic_save", "pic_restore", "pic_get_config", "pic_set_rr", "pic_shard_runs")
 NOALLOC_MAX_BINS = 65536
 
 
@@ -200,6 +200,8 @@ def library():
         L.pic_restore.argtypes = [C.c_char_p, C.c_int, C.c_int, C.POINTER(vp)]
         L.pic_get_config.argtypes = [vp, C.POINTER(Config)]
         L.pic_set_rr.argtypes = [vp, C.c_int]
+        L.pic_shard_runs.argtypes = [C.POINTER(Config), C.POINTER(RunDesc), C.c_int, C.c_int, C.c_int, C.c_size_t,
+                                     C.POINTER(C.c_int), dp]
         L.pic_server_cancel.argtypes = [vp, i64]
         L.pic_snapshot.argtypes = [vp, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp, C.POINTER(i64)]
         L.pic_batch_snapshot.argtypes = [vp, C.c_int, C.c_int, C.c_double, i64, dp, dp, dp, dp, dp, dp,
@@ -241,6 +243,21 @@ def electron_scan(cases, integrator=INTEGRATOR_RK4, rr=True, deriv=False, dt=0.0
     if rc != 0:
         raise PicError(rc, library().pic_last_error(None).decode())
     return out
+
+
+def shard_runs(descs, n_ranks, cells_per_lambda, in_order=False, budget_per_rank=0, cfl=0.95):
+    """pic_shard_runs: the rank of each run (list of RunDesc) and the
+    particle-steps assigned to each rank."""
+    L = library()
+    n = len(descs)
+    arr = (RunDesc * max(1, n))(*descs)
+    cfg = Config(1.0, cells_per_lambda, cfl, 0.8, 1, 8, 1, 0, 8, 0)
+    ranks = (C.c_int * max(1, n))()
+    work = np.zeros(n_ranks)
+    rc = L.pic_shard_runs(C.byref(cfg), arr, n, n_ranks, int(bool(in_order)), budget_per_rank, ranks, _dp(work))
+    if rc != 0:
+        raise PicError(rc, L.pic_last_error(None).decode())
+    return [ranks[i] for i in range(n)], work
 
 
 def spectrum_noalloc(px_ptr, py_ptr, pz_ptr, n, mass_me, weight_dx, nbins, e_min, e_max, counts_ptr,

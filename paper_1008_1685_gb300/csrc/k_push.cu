@@ -18,12 +18,14 @@
 // shapes: the old bin's share up to the crossing point, the new bin's after
 // it).  Determinism: a thread first adds the records of its successive
 // particles that share an anchor, in a fixed order; the record is then
-// converted to 32-bit fixed point and the lanes of a warp holding the same
-// anchor are summed exactly with an integer warp reduction (match + reduce),
-// whose total is shifted to the 64-bit scale of the accumulators and added
-// with one integer atomic per value, first into shared memory, then into
-// global memory.  Integer addition is exact and associative, so the result
-// does not depend on the order in which lanes, warps or CTAs arrive.
+// converted to 32-bit fixed point and added to the unit's window in shared
+// memory with integer atomics, which hold exact 64-bit sums as pairs of 32-bit
+// words (when all lanes of a warp hold the same anchor, as in dense plasma,
+// the lanes are first summed exactly by an integer warp reduction).  At the
+// end the window is shifted to the 64-bit scale of the accumulators and added
+// to global memory with integer atomics.  Integer addition is exact and
+// associative, so the result does not depend on the order in which lanes,
+// warps or CTAs arrive.
 #include "picrr_internal.cuh"
 
 namespace picrr {
@@ -32,26 +34,70 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Add one stencil record per lane: lanes with equal anchors are summed
-// exactly in 32-bit fixed point (2^lscale units, |value| < 2^26 per lane), the
-// sums are shifted to the accumulators' 2^fp units and added by the group's
-// first lane to Jy and Jz on nodes key..key+2 and Jx on half nodes key, key+1.
-// key < 0 marks an empty record.
-__device__ __forceinline__ void warp_add(int key, const float (&v)[8], unsigned long long (*sJ)[WMAX], float lscale,
-                                         int shift) {
-    const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(FULL, key);
-    int t[8];
+#ifndef PICRR_THIN_PER_CELL
+#define PICRR_THIN_PER_CELL 8
+#endif
+// Units with fewer particles per cell than this (thinly spread plasma, where
+// nearly every lane of a warp holds its own anchor) skip the warp-wide test
+// of warp_add altogether: every lane adds its records by itself.
+constexpr int kThinPerCell = PICRR_THIN_PER_CELL;
+
+// The unit's current window in shared memory holds exact 64-bit integer sums
+// (in the 2^lscale units of the records) as two 32-bit words, lo (unsigned)
+// and hi (signed): value = hi * 2^32 + lo.  A signed 32-bit term t is added
+// with a 32-bit atomic on lo, which returns the old word: the addition
+// wrapped (carried) iff the new word is below the old one, and hi then gets
+// sign(t) + carry (-1, 0 or +1; nothing in most cases).  Every carry is seen by
+// exactly one adder, so the pair always holds the exact sum, in any order.
+// (A 64-bit shared-memory atomic runs at a sixth of the 32-bit rate.)
+struct Window {
+    unsigned lo[3][WMAX];  // Jx (half nodes), Jy, Jz (nodes)
+    int hi[3][WMAX];
+};
+
+__device__ __forceinline__ void win_add(Window& w, int comp, int at, int t) {
+    const unsigned old = atomicAdd(&w.lo[comp][at], static_cast<unsigned>(t));
+    const int h = (t < 0 ? -1 : 0) + (old + static_cast<unsigned>(t) < old ? 1 : 0);
+    if (h) atomicAdd(&w.hi[comp][at], h);
+}
+
+// Position of value q of a stencil record anchored at key: q 0..2 are Jy at
+// key+q, 3..5 Jz at key+q-3, 6 and 7 Jx at half nodes key, key+1.
+__device__ __forceinline__ int rec_comp(int q) { return q < 3 ? 1 : (q < 6 ? 2 : 0); }
+__device__ __forceinline__ int rec_at(int key, int q) { return key + (q < 3 ? q : (q < 6 ? q - 3 : q - 6)); }
+
+// One lane's record added by itself: each nonzero value in 32-bit fixed
+// point (2^lscale units, |value| < 2^26).
+__device__ __forceinline__ void lane_add(int key, const float (&v)[8], Window& w, float lscale) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t[q] = __reduce_add_sync(peers, __float2int_rn(v[q] * lscale));
-    if (key >= 0 && lane == __ffs(peers) - 1) {
+    for (int q = 0; q < 8; ++q) {
+        const int t = __float2int_rn(v[q] * lscale);
+        if (t) win_add(w, rec_comp(q), rec_at(key, q), t);
+    }
+}
+
+// One stencil record per lane (key < 0: none).  When every lane holds the
+// same anchor (dense plasma), the records are summed exactly in 32-bit fixed
+// point (|value| < 2^26 per lane, so the warp sum fits) by one integer warp
+// reduction per value and lane 0 adds the sums; otherwise every lane adds its
+// own record.  (A reduction over lanes grouped by anchor runs once per
+// distinct anchor, which costs more than the lanes' own atomics as soon as
+// the warp holds two.)
+__device__ __forceinline__ void warp_add(int key, const float (&v)[8], Window& w, float lscale) {
+    const int k0 = __shfl_sync(FULL, key, 0);
+    if (__all_sync(FULL, key == k0)) {
+        if (k0 >= 0) {
+            int t[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            // q 0..2: Jy at key+q; 3..5: Jz at key+q-3; 6, 7: Jx at key, key+1
-            const int comp = q < 3 ? 1 : (q < 6 ? 2 : 0);
-            const int at = key + (q < 3 ? q : (q < 6 ? q - 3 : q - 6));
-            if (t[q]) atomicAdd(&sJ[comp][at], static_cast<unsigned long long>(static_cast<long long>(t[q]) << shift));
+            for (int q = 0; q < 8; ++q) t[q] = __reduce_add_sync(FULL, __float2int_rn(v[q] * lscale));
+            if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (t[q]) win_add(w, rec_comp(q), rec_at(k0, q), t[q]);
+            }
         }
+    } else if (key >= 0) {
+        lane_add(key, v, w, lscale);
     }
 }
 
@@ -110,7 +156,7 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
     using I = typename Slot<W>::I;
     using F = typename Slot<W>::F;
     __shared__ __align__(128) float sF[5][WMAX];
-    __shared__ __align__(16) unsigned long long sJ[3][WMAX];  // Jx (half nodes), Jy, Jz (nodes) of the window
+    __shared__ __align__(16) Window sJ;  // the unit's current: Jx (half nodes), Jy, Jz (nodes) of the window
     __shared__ __align__(8) uint64_t bar;
     __shared__ double sred[PUSH_T / 32];
 
@@ -136,7 +182,10 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
         return;
     }
 
-    for (int i = tid; i < 3 * WMAX; i += PUSH_T) (&sJ[0][0])[i] = 0ull;
+    for (int i = tid; i < 3 * WMAX; i += PUSH_T) {
+        (&sJ.lo[0][0])[i] = 0u;
+        (&sJ.hi[0][0])[i] = 0;
+    }
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -175,6 +224,7 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
         return;
     }
 
+    const bool thin = end - start < kThinPerCell * (hi - lo + 1);  // block-uniform
     float rad = 0.f;
     int rk = -1;  // running stencil record of this thread (anchor rk)
     float rv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -308,8 +358,14 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
             }
             // merge the particle's record into this thread's running record
             const bool merge = ka < 0 || rk < 0 || ka == rk;
-            if (__any_sync(FULL, !merge)) {
-                warp_add(merge ? -1 : rk, rv, sJ, lscale, shift);
+            if (thin) {
+                if (!merge) {
+                    lane_add(rk, rv, sJ, lscale);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) rv[q] = 0.f;
+                }
+            } else if (__any_sync(FULL, !merge)) {
+                warp_add(merge ? -1 : rk, rv, sJ, lscale);
                 if (!merge) {
                     rk = -1;
 #pragma unroll
@@ -328,7 +384,11 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
             qy[j] = py;
             qz[j] = pz;
         }
-        warp_add(rk, rv, sJ, lscale, shift);
+        if (thin) {
+            if (rk >= 0) lane_add(rk, rv, sJ, lscale);
+        } else {
+            warp_add(rk, rv, sJ, lscale);
+        }
         rk = -1;
 #pragma unroll
         for (int q = 0; q < 8; ++q) rv[q] = 0.f;
@@ -365,12 +425,14 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
         for (int w = 0; w < PUSH_T / 32; ++w) t += sred[w];
         P.rad_part[u] += t * static_cast<double>(R.rad_w[s]);  // summed into the tally at the next flush
     }
-    // flush the window
+    // flush the window: each exact sum shifted from record units to the
+    // accumulators' 2^fp units (the run's fixed-point scale keeps it in range)
     for (int i = tid; i < L; i += PUSH_T) {
-        const unsigned long long jx = sJ[0][i], jy = sJ[1][i], jz = sJ[2][i];
-        if (jx) atomicAdd(R.J[par][0] + p0 + i, jx);
-        if (jy) atomicAdd(R.J[par][1] + p0 + i, jy);
-        if (jz) atomicAdd(R.J[par][2] + p0 + i, jz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long v = static_cast<long long>((static_cast<unsigned long long>(static_cast<unsigned>(sJ.hi[c][i])) << 32) | sJ.lo[c][i]);
+            if (v) atomicAdd(R.J[par][c] + p0 + i, static_cast<unsigned long long>(v) << shift);
+        }
     }
 }
 

@@ -511,8 +511,8 @@ size_t rounded(size_t bytes) { return ((bytes ? bytes : 16) + 255) & ~static_cas
 // batch: its grid, sort scratch and particle buffers as run_open and
 // alloc_species allocate them, plus its share of the batch's unit table and
 // Yee block table with the unit table's growth factor (1.5).
-size_t run_footprint(const Batch* b, double length_lambda, int64_t n) {
-    const int64_t Nx = std::llround(length_lambda * b->cfg.cells_per_lambda);
+size_t run_footprint_cpl(double cells_per_lambda, double length_lambda, int64_t n) {
+    const int64_t Nx = std::llround(length_lambda * cells_per_lambda);
     const size_t glen = (static_cast<size_t>(Nx) + 1 + 2 * PADF + 4 + 3) / 4 * 4;
     size_t t = 10 * rounded(glen * 4) + 6 * rounded(glen * 8) + 3 * rounded(glen * 4) + rounded(32);
     const size_t nk = static_cast<size_t>(Nx) + 2, nkb = static_cast<size_t>(Nx) / KEY_T + 2,
@@ -525,6 +525,10 @@ size_t run_footprint(const Batch* b, double length_lambda, int64_t n) {
     t += units * (6 * 4 + 8 + 2 * SSTR * 4) * 3 / 2;
     t += static_cast<size_t>(Nx / FIELD_T + 1) * 8 * 3 / 2;
     return t;
+}
+
+size_t run_footprint(const Batch* b, double length_lambda, int64_t n) {
+    return run_footprint_cpl(b->cfg.cells_per_lambda, length_lambda, n);
 }
 
 void run_release(Batch* b, int id) {
@@ -2064,6 +2068,50 @@ pic_status pic_batch_run_footprint(const pic_batch* h, const pic_run_desc* d, si
         return fail(nullptr, PIC_ERR_INVALID_ARG, "need 16 <= cells <= 1e9, ppc >= 1, thickness > 0");
     const int64_t n = std::llround(d->foil_thickness_lambda * cpl) * static_cast<int64_t>(d->ppc);
     *bytes = run_footprint(h->b, d->length_lambda, n);
+    return PIC_OK;
+}
+
+pic_status pic_shard_runs(const pic_config* common, const pic_run_desc* runs, int n_runs, int n_ranks,
+                          int in_order, size_t budget_per_rank, int* rank_of_run, double* work_per_rank) {
+    if (!common || (n_runs > 0 && (!runs || !rank_of_run)) || n_runs < 0 || n_ranks < 1)
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "need a config, n_runs >= 0 runs and ranks, n_ranks >= 1");
+    const double cpl = common->cells_per_lambda;
+    if (!(cpl > 0.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "cells_per_lambda must be > 0");
+    std::vector<double> work(static_cast<size_t>(n_runs));
+    std::vector<size_t> foot(static_cast<size_t>(n_runs));
+    for (int i = 0; i < n_runs; ++i) {
+        const pic_run_desc& d = runs[i];
+        const double ncell = d.length_lambda * cpl;
+        if (!(d.length_lambda > 0.0) || !(ncell >= 16.0 && ncell <= 1.0e9) || d.ppc < 1 ||
+            !(d.foil_thickness_lambda > 0.0) || !(d.foil_thickness_lambda * cpl < 1.0e9) || d.steps < 1)
+            return fail(nullptr, PIC_ERR_INVALID_ARG,
+                        "run " + std::to_string(i) + ": need 16 <= cells <= 1e9, ppc >= 1, thickness > 0, steps >= 1");
+        const int64_t n = std::llround(d.foil_thickness_lambda * cpl) * static_cast<int64_t>(d.ppc);
+        work[i] = 2.0 * static_cast<double>(n) * static_cast<double>(d.steps);
+        foot[i] = run_footprint_cpl(cpl, d.length_lambda, n);
+    }
+    std::vector<int> order(static_cast<size_t>(n_runs));
+    for (int i = 0; i < n_runs; ++i) order[i] = i;
+    if (!in_order)  // largest work first; equal work keeps the index order
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(static_cast<size_t>(n_ranks), 0.0);
+    std::vector<size_t> mem(static_cast<size_t>(n_ranks), 0);
+    std::vector<int> out(static_cast<size_t>(n_runs), -1);
+    for (int i : order) {
+        int best = -1;
+        for (int r = 0; r < n_ranks; ++r) {
+            if (budget_per_rank && mem[r] + foot[i] > budget_per_rank) continue;
+            if (best < 0 || load[r] < load[best]) best = r;  // ties: the lowest rank
+        }
+        if (best < 0)
+            return fail(nullptr, PIC_ERR_OOM, "run " + std::to_string(i) + " fits no rank's memory budget");
+        out[i] = best;
+        load[best] += work[i];
+        mem[best] += foot[i];
+    }
+    for (int i = 0; i < n_runs; ++i) rank_of_run[i] = out[i];
+    if (work_per_rank)
+        for (int r = 0; r < n_ranks; ++r) work_per_rank[r] = load[r];
     return PIC_OK;
 }
 

@@ -271,3 +271,30 @@ def test_set_shapes_changes_only_rounding(picrr):
     with pytest.raises(picrr.PicError):
         g = picrr.Sim(length_lambda=4, cells_per_lambda=CPL)
         g.set_shapes(3000, 8, 4)
+
+
+def test_scan_split_over_ranks_gives_the_same_runs(picrr):
+    """A scan split over two GPUs by pic_shard_runs (here the two shares run
+    one after the other on this GPU, as two batches) gives every run the same
+    result as the whole scan in one batch: the split changes only which runs
+    share a batch."""
+    descs = RUNS + [EARLY, LATE] + [dict(d, seed=d["seed"] + 20, steps=d["steps"] // 2 + 8) for d in RUNS]
+    rd = [picrr.run_desc(d["length_lambda"], d["foil_x0"], d["foil_thickness"], d["ne"], d["a0"], d["polarization"],
+                         d["duration"], d["steps"], rr_on=d["rr_on"], ppc=d["ppc"], seed=d["seed"]) for d in descs]
+    ranks, work = picrr.shard_runs(rd, 2, CPL)
+    assert set(ranks) == {0, 1}
+
+    def run(subset):
+        b = picrr.Batch(CPL, max_runs=len(subset), sort_interval=8)
+        ids = {i: add(b, descs[i]) for i in subset}
+        while b.step(500) > 0:
+            pass
+        out = {i: batch_snapshot(b, r) for i, r in ids.items()}
+        b.close()
+        return out
+
+    whole = run(list(range(len(descs))))
+    for rank in (0, 1):
+        part = run([i for i, r in enumerate(ranks) if r == rank])
+        for i, snap in part.items():
+            assert_same(snap, whole[i], (rank, i))

@@ -307,3 +307,20 @@ def test_empty_and_single_species(picrr):
     o.step(40)
     check_momenta(g.particles(0), o.particles(0), 5.0, g.dt, tol=1e-4)
     assert g.particles(1)["x"].size == 0
+
+
+def test_gpu_foil_generator_is_the_published_splitmix64(picrr):
+    """The CUDA foil loader draws the same published SplitMix64 outputs as the
+    oracle's (cells 0..4 of a one-particle-per-cell foil from cell 0, seed
+    1234567): each offset is the output's top 24 bits over 2^24."""
+    import json
+    import os
+
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "splitmix64_published.json")))
+    g = picrr.Sim(length_lambda=1.0, cells_per_lambda=64, seed=gold["seed"])
+    g.load_foil(0.0, 0.25, 1.0, 1, 1.0, 1)
+    xi = g.particles(0)["x"] / g.dx
+    g.close()
+    for c, out in enumerate(gold["outputs"]):
+        assert round((xi[c] - c) * 2 ** 24) == int(out) >> 40, c

@@ -84,20 +84,23 @@ def test_sort_interval_64_with_particles_frozen_at_both_walls(picrr, shapes):
     assert g.stats()["sort_count"] == 2
 
 
-def dense_foil_pair(picrr):
+FSCALE = 10.0
+
+
+def dense_foil_pair(picrr, shapes=(16384, 64, 4)):
     g, o = pair(picrr, length_lambda=5, cells_per_lambda=200, rr_on=True)
     nx = g.nx
-    F = synth.random_fields(nx, scale=40.0, seed=8)
+    F = synth.random_fields(nx, scale=FSCALE, seed=8)
     for s in (g, o):
         s.set_fields(*F)
     # about 2500 particles per cell per species in cells 300..700: 62 units of
     # at most 16384 particles per species, each spanning about 7 cells
-    for sp, (n, q, m, w, ps) in enumerate([(1_000_003, -1.0, 1.0, 0.002, 30.0),
-                                           (999_997, 1.0, 1836.15267343, 0.002, 1.0)]):
+    for sp, (n, q, m, w, ps) in enumerate([(1_000_003, -1.0, 1.0, 0.0005, 30.0),
+                                           (999_997, 1.0, 1836.15267343, 0.0005, 1.0)]):
         cell, off, px, py, pz = synth.random_particles(n, 300, 700, pscale=ps, seed=30 + sp)
         for s in (g, o):
             s.load_particles(sp, cell, off, px, py, pz, w, q, m)
-    g.set_shapes(16384, 64, 4)
+    g.set_shapes(*shapes)
     return g, o
 
 
@@ -108,7 +111,7 @@ def test_tuned_shapes_dense_foil_one_step(picrr):
     o.step(1)
     for sp in (0, 1):
         pg, po = g.particles(sp), o.particles(sp)
-        assert np.max(momentum_err(pg, po, 40.0, g.dt)) <= 1e-5
+        assert np.max(momentum_err(pg, po, FSCALE, g.dt)) <= 1e-5
         assert np.max(np.abs(pg["x"] - po["x"])) <= 2e-6 * g.dx
         assert np.array_equal(pg["flag"], po["flag"])
     for comp in range(8):
@@ -119,22 +122,35 @@ def test_tuned_shapes_dense_foil_through_a_whole_sort_interval(picrr):
     """64 steps at sort interval 64: the last push stages windows 63 steps
     wide on each side of its units (electrons with |p| ~ 30 cross up to 60
     cells in that time); every particle and all 8 grid components (the
-    current of step 64) against the oracle."""
-    g, o = dense_foil_pair(picrr)
-    g.step(64)
-    o.step(64)
-    assert g.stats()["sort_count"] == 1
-    worst = {}
-    for sp in (0, 1):
-        pg, po = g.particles(sp), o.particles(sp)
-        worst["p%d" % sp] = float(np.max(momentum_err(pg, po, 40.0, g.dt)))
-        worst["x%d" % sp] = float(np.max(np.abs(pg["x"] - po["x"])) / g.dx)
-        assert np.array_equal(pg["flag"], po["flag"])
-    for comp in range(8):
-        worst["f%d" % comp] = float(rel_l2(g.field(comp), o.field(comp)))
-    assert worst["p0"] <= 2e-4 and worst["p1"] <= 2e-4, worst
-    assert worst["x0"] <= 2e-5 and worst["x1"] <= 2e-5, worst
-    assert max(worst["f%d" % c] for c in range(8)) <= 1e-4, worst
+    current of step 64) against the oracle, at the tuned shapes and at the
+    default ones (units of 4096, sort every 8 steps, 2 per thread).  Over 64
+    steps the single-precision rounding grows with the dynamics: perturbing
+    the oracle's own initial momenta by 6e-8 (relative) moves them by up to
+    2e-6 and the positions by 3e-5 cells in a 200k-particle version of this
+    case, so each particle is held to 2e-4 and 1e-3 cells (a field window misplaced by even one cell changes momenta by
+    about 1e-2 in this field)."""
+    o = None
+    for shapes in ((16384, 64, 4), (4096, 8, 2)):
+        g, o2 = dense_foil_pair(picrr, shapes)
+        if o is None:
+            o = o2
+            o.step(64)
+            ref = [o.particles(sp) for sp in (0, 1)]
+            fref = [o.field(c) for c in range(8)]
+        g.step(64)
+        assert g.stats()["sort_count"] == 64 // shapes[1]
+        worst = {}
+        for sp in (0, 1):
+            pg, po = g.particles(sp), ref[sp]
+            worst["p%d" % sp] = float(np.max(momentum_err(pg, po, FSCALE, g.dt)))
+            worst["x%d" % sp] = float(np.max(np.abs(pg["x"] - po["x"])) / g.dx)
+            assert np.array_equal(pg["flag"], po["flag"])
+        for comp in range(8):
+            worst["f%d" % comp] = float(rel_l2(g.field(comp), fref[comp]))
+        g.close()
+        assert worst["p0"] <= 2e-4 and worst["p1"] <= 2e-4, (shapes, worst)
+        assert worst["x0"] <= 1e-3 and worst["x1"] <= 1e-3, (shapes, worst)
+        assert max(worst["f%d" % c] for c in range(8)) <= 1e-4, (shapes, worst)
 
 
 def test_set_rr_switches_the_kick(picrr):
