@@ -9,8 +9,10 @@
 // needs from its neighbours' old data, so one launch does the whole step
 // (old and new fields live in separate buffers).  The block also converts
 // the fixed-point current to float, zeroes the accumulators of the next
-// step, adds the exact discrete Poynting flux through the two accounting
-// planes.
+// step and adds the exact discrete Poynting flux through the two accounting
+// planes.  (A version without shared memory and barriers, each thread
+// recomputing the half-step B and new E it shares with its neighbours from
+// global loads, ran at half the speed.)
 #include "picrr_internal.cuh"
 
 namespace picrr {
@@ -119,8 +121,6 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
         if (i <= Nx) {
             Fn[1][pi] = nEy[q + 1];
             Fn[2][pi] = nEz[q + 1];
-            R.Jf[1][pi] = sJy[q + 1];
-            R.Jf[2][pi] = sJz[q + 1];
         }
         if (i < Nx) {
             float by = hBy[q + 2] + hc * (nEz[q + 2] - nEz[q + 1]);
@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(FIELD_T) k_field(const FieldParams P) {
             Fn[3][pi] = by;
             Fn[4][pi] = bz;
             const float jx = fix_to_float(Jacc[0][pi], fpi, fph);
-            R.Jf[0][pi] = jx;
             Fn[0][pi] = Fo[0][pi] - fdt * jx;
         }
         // exact discrete Poynting flux through the accounting planes

@@ -483,7 +483,6 @@ pic_status run_open(Batch* b, double length_lambda, int source_node, int rr_on, 
         for (int c = 0; c < 5 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.F[x][c], r.glen);
     for (int x = 0; x < 2 && st == PIC_OK; ++x)
         for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.J[x][c], r.glen);
-    for (int c = 0; c < 3 && st == PIC_OK; ++c) st = dalloc_t(b, r.mem, &d.Jf[c], r.glen);
     if (st == PIC_OK) st = dalloc_t(b, r.mem, &d.tally, 4);
     const size_t nk = static_cast<size_t>(Nx) + 2, nkb = static_cast<size_t>(Nx) / KEY_T + 2,
                  ntl = static_cast<size_t>(Nx) / TILE + 3;
@@ -1539,6 +1538,21 @@ pic_status run_snapshot(Batch* b, int id, int species, double chi_flag, int64_t 
     return PIC_OK;
 }
 
+// The current of a run's last step, component c (Jx, Jy, Jz), on the whole
+// padded grid: its fixed-point accumulators (the set of the last step, kept
+// until the next step's Yee update zeroes it) times 2^-fp.  Before the first
+// step that set holds zeros, or the current a checkpoint restored into it.
+pic_status last_current(Batch* b, const RunHost& r, int c, std::vector<double>& out) {
+    const int lp = 1 - run_fbuf(b, r);
+    std::vector<long long> h(r.glen);
+    PIC_CK(b, cudaMemcpyAsync(h.data(), r.dev.J[lp][c], sizeof(long long) * r.glen, cudaMemcpyDeviceToHost,
+                              b->stream));
+    PIC_CK(b, cudaStreamSynchronize(b->stream));
+    out.resize(r.glen);
+    for (size_t i = 0; i < r.glen; ++i) out[i] = std::ldexp(static_cast<double>(h[i]), -r.fp_bits);
+    return PIC_OK;
+}
+
 pic_status run_read_fields(Batch* b, int id, int comp, int64_t cap, double* out, int64_t* nout) {
     if (comp < PIC_EX || comp > PIC_JZ) return fail(b, PIC_ERR_INVALID_ARG, "bad component");
     const RunHost& r = b->runs[id];
@@ -1546,7 +1560,14 @@ pic_status run_read_fields(Batch* b, int id, int comp, int64_t cap, double* out,
     const int64_t n = node ? r.Nx + 1 : r.Nx;
     if (nout) *nout = n;
     if (!out || cap < n) return fail(b, PIC_ERR_INVALID_ARG, "output too small");
-    const float* src = comp <= PIC_BZ ? r.dev.F[run_fbuf(b, r)][comp] : r.dev.Jf[comp - PIC_JX];
+    if (comp >= PIC_JX) {
+        std::vector<double> j;
+        pic_status st = last_current(b, r, comp - PIC_JX, j);
+        if (st != PIC_OK) return st;
+        for (int64_t i = 0; i < n; ++i) out[i] = j[static_cast<size_t>(PADF + i)];
+        return PIC_OK;
+    }
+    const float* src = r.dev.F[run_fbuf(b, r)][comp];
     std::vector<float> h(static_cast<size_t>(n));
     PIC_CK(b, cudaMemcpyAsync(h.data(), src + PADF, sizeof(float) * n, cudaMemcpyDeviceToHost, b->stream));
     PIC_CK(b, cudaStreamSynchronize(b->stream));
@@ -1615,7 +1636,15 @@ pic_status run_save(Batch* b, int id, const char* path) {
     bool ok = (e = cudaStreamSynchronize(b->stream)) == cudaSuccess && std::fwrite(&h, sizeof(h), 1, f) == 1;
     const int fb = run_fbuf(b, r), pb = run_pbuf(b, r);
     for (int c = 0; c < 5 && ok; ++c) ok = put(r.dev.F[fb][c], r.glen * 4);
-    for (int c = 0; c < 3 && ok; ++c) ok = put(r.dev.Jf[c], r.glen * 4);
+    for (int c = 0; c < 3 && ok; ++c) {  // the last step's current, as float
+        std::vector<double> j;
+        if (last_current(b, r, c, j) != PIC_OK) {
+            ok = false;
+            break;
+        }
+        std::vector<float> jf(j.begin(), j.end());
+        ok = std::fwrite(jf.data(), 4, jf.size(), f) == jf.size();
+    }
     for (int s = 0; s < 2 && ok; ++s) {
         if (!h.loaded[s] || h.n[s] == 0) continue;
         const DevSpecies& d = r.dev.sp[s][pb];
@@ -1646,7 +1675,9 @@ pic_status run_restore(Batch* b, int id, FILE* f, const CkHeader& h) {
     };
     pic_status st = PIC_OK;
     for (int c = 0; c < 5 && st == PIC_OK; ++c) st = get(r.dev.F[0][c], r.glen * 4);
-    for (int c = 0; c < 3 && st == PIC_OK; ++c) st = get(r.dev.Jf[c], r.glen * 4);
+    std::vector<float> jsaved(3 * r.glen);
+    if (std::fread(jsaved.data(), 4, jsaved.size(), f) != jsaved.size())
+        return fail(b, PIC_ERR_INVALID_ARG, "checkpoint file is truncated");
     for (int s = 0; s < 2 && st == PIC_OK; ++s) {
         if (!h.loaded[s]) continue;
         if ((st = alloc_species(b, r, s, h.n[s])) != PIC_OK) break;
@@ -1673,6 +1704,15 @@ pic_status run_restore(Batch* b, int id, FILE* f, const CkHeader& h) {
     }
     r.fields_set = true;
     r.t_offset = h.steps;
+    // the saved current goes into the accumulator set a run reads back before
+    // its first step (1), in the fixed-point scale the run will step with
+    finalize_run_params(b, r);
+    std::vector<long long> acc(r.glen);
+    for (int c = 0; c < 3; ++c) {
+        for (size_t i = 0; i < r.glen; ++i)
+            acc[i] = std::llround(std::ldexp(static_cast<double>(jsaved[c * r.glen + i]), r.fp_bits));
+        PIC_CK(b, cudaMemcpy(r.dev.J[1][c], acc.data(), sizeof(long long) * r.glen, cudaMemcpyHostToDevice));
+    }
     return PIC_OK;
 }
 

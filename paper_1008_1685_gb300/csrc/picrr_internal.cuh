@@ -10,7 +10,9 @@
 //                 PADF holds node / half node 0; the guard elements are zero.
 //                 Ex, Ey, Ez, By, Bz are ping-ponged by the Yee kernel.
 //   accumulators  int64 fixed point (2^fp units) for Jx (half nodes) and
-//                 Jy, Jz (nodes), two sets alternating by step parity.
+//                 Jy, Jz (nodes), two sets alternating by step parity; the
+//                 set of the last step holds its current until the next
+//                 step's Yee update zeroes it (read-back converts it).
 //   particles     per species, structure of arrays, two buffers each
 //                 (ping-ponged by the sort): cell int32, off/px/py/pz float,
 //                 id int32.  A particle that left the box is frozen at the
@@ -83,7 +85,6 @@ struct RunDev {
     float fp_inv;          // 2^-fp of the current accumulators
     float* F[2][5];        // [buffer][Ex, Ey, Ez, By, Bz], padded
     unsigned long long* J[2][3];  // [parity][Jx, Jy, Jz], padded
-    float* Jf[3];          // float J of the last step (read-back)
     double* tally;         // [4]: radiated, flux in, flux out, spare
     int32_t* keycount[2];  // sort scratch per species: [Nx + 2]
     int32_t* keystart[2];  // [Nx + 2]; keystart[Nx] = particles

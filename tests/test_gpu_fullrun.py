@@ -98,8 +98,9 @@ def test_small_run_seed_ensembles_within_2_percent(picrr):
 
 PAPER_KW = dict(length_lambda=60, cells_per_lambda=1000, cfl=0.95, lambda_um=0.8, source_node=8)
 PAPER_CASES = [(a0, pol, rr) for a0 in (200.0, 350.0, 500.0) for pol in (0, 1) for rr in (True, False)]
-# the pulse front reaches the foil (node 100) after ~97 steps; 150 steps: driven, not yet chaotic
-EARLY_STEPS = 150
+# the pulse front reaches the foil (node 100) after ~97 steps; by step 250 the
+# rising front (a ~ 0.5 a0 in vacuum) has driven the skin layer relativistically
+EARLY_STEPS = 250
 
 
 def oracle_paper_scale(case):
@@ -123,8 +124,8 @@ def test_paper_scale_grid_first_500_steps(picrr):
     """The paper-scale grid (60,000 cells, 400 + 400 particles per cell) for
     a0 in {200, 350, 500}, LP and CP, RR on and off: fields after 500 steps
     within 1e-4 (relative L2 per group) and electron momenta within 1e-4 in
-    the median, and every electron's momentum after the first 150 steps (the
-    front has then driven the skin layer for ~50 steps) within 1e-4 in the
+    the median, and every electron's momentum after the first 250 steps (the
+    front has then driven the skin layer for ~150 steps) within 1e-4 in the
     R12 norm.  A 0.6-period sin^2 pulse peaks 0.3 periods (300 cells) behind
     its front, so its peak reaches the foil inside the window."""
     import concurrent.futures as cf
@@ -141,10 +142,10 @@ def test_paper_scale_grid_first_500_steps(picrr):
         e = g.particles(0)
         pg = np.stack([e["px"], e["py"], e["pz"]], 1)
         po = np.stack(o["early"], 1)
-        assert np.max(np.abs(po)) > 0.01 * a0  # the front has reached the skin layer
         scale = np.maximum(np.linalg.norm(po, axis=1), 1e-3 * a0 * g.dt)
         err = np.max(np.abs(pg - po), axis=1) / scale
-        assert np.max(err) <= 1e-4, (a0, pol, rr, float(np.max(err)), int(np.argmax(err)))
+        assert np.max(err) <= 1e-4, (a0, pol, rr, float(np.max(err)), float(np.max(np.abs(po))))
+        assert np.max(np.abs(po)) > 1.0  # the front has driven the skin layer relativistically
         g.step(500 - EARLY_STEPS)
         for comps in ((picrr.EY, picrr.EZ), (picrr.BY, picrr.BZ), (picrr.EX,)):
             a = np.concatenate([g.field(c) for c in comps])
