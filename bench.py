@@ -46,12 +46,14 @@ PULSE_AT_FOIL_STEP = int(math.ceil((LARGE["foil_x0"] * LARGE["cells_per_lambda"]
                                    / LARGE["cfl"]))
 BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int32 + 4 x fp32)
 # DRAM traffic of one push launch of this workload, measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, 64M particles)
-# with the pulse in the foil, keyed by (particles, particles per unit, sort
-# interval, particles per thread, timed window's first step rounded down to
-# 100, digest of the push kernel's source); a run that does not match every
-# key, or a kernel changed since the capture, reports null
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch, 64M particles,
+# the push of step 1996) with the pulse in the foil, keyed by (particles,
+# particles per unit, sort interval, particles per thread, whether the timed
+# window starts after the pulse reached the foil, digest of the push
+# kernel's source); a run that does not match every key, or a kernel changed
+# since the capture, reports null
 PUSH_TRAFFIC = {
+    (64_000_000, 16384, 64, 4, True, "c69fad8aa597"): 1_280_352_512 + 1_219_084_288,
 }
 
 
@@ -108,7 +110,7 @@ def rr_cost_leg(sim, interval, reps=3):
 # the batched scan: 256 independent runs, 30 lambda at lambda/500 (15,000 cells), foil front at
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
 SCAN = dict(n_runs=256, length_lambda=30.0, cells_per_lambda=500.0, cfl=0.95, foil_x0=10.0, periods=40.0,
-            duration=20.0, seed_base=1000, sort_interval=8)
+            duration=20.0, seed_base=1000, sort_interval=8, shapes=(8192, 64, 2))
 
 
 def scan_steps(periods, w=SCAN):
@@ -136,7 +138,7 @@ def desc_particles(d, cpl):
 # particles per species, 20..200 periods, physical parameters as in the scan,
 # admission by device memory under a 150 GB budget
 SERVE = dict(rate=20.0, window_s=10.0, cap_s=40.0, budget=150 * 10**9, max_runs=256, chunk=64, seed=77,
-             policy="sjf", resident=24_000_000)
+             policy="sjf", resident=24_000_000, sort_interval=64)
 # a second stream at a rate one GB300 keeps up with for this mix (its capacity is about 1 request/s)
 SERVE_LOW = dict(SERVE, rate=0.5, window_s=20.0, cap_s=40.0)
 
@@ -192,7 +194,7 @@ def serve_leg(picrr, device, cfg=SERVE, w=SCAN, rank=0, ws=1):
 
     reqs = my_requests(picrr, cfg, w, rank, ws)
     srv = picrr.Server(w["cells_per_lambda"], max_runs=cfg["max_runs"], chunk_steps=cfg["chunk"], cfl=w["cfl"],
-                       sort_interval=w["sort_interval"], device=device, hbm_budget_bytes=cfg["budget"])
+                       sort_interval=cfg["sort_interval"], device=device, hbm_budget_bytes=cfg["budget"])
     srv.set_policy(picrr.SERVE_SHORTEST_FIRST if cfg["policy"] == "sjf" else picrr.SERVE_FIFO, cfg["resident"])
     tickets = []
     t0 = time.perf_counter()
@@ -247,7 +249,7 @@ def plain_serve_leg(picrr, device, cfg=SERVE, w=SCAN, rank=0, ws=1):
         j = min(arrived, key=lambda q: (work[q], q)) if cfg["policy"] == "sjf" else arrived[0]
         ta, d = reqs[j]
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
-                      sort_interval=w["sort_interval"], seed=d["seed"], device=device)
+                      sort_interval=cfg["sort_interval"], seed=d["seed"], device=device)
         s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
         s.inject_laser(d["a0"], d["polarization"], 0, d["duration"])
         left = d["steps"]
@@ -273,18 +275,20 @@ def shard(picrr, descs, ranks, in_order=False, w=SCAN):
     return picrr.shard_runs(rd, ranks, w["cells_per_lambda"], in_order=in_order)
 
 
-def batched_scan(picrr, device, run_ids, w=SCAN, max_steps=None):
+def batched_scan(picrr, device, run_ids, w=SCAN, max_steps=None, shapes=None):
     """The scan runs run_ids (indices into the scan's seed sequence) in one
     batch (one launch per kernel per step for all of them), from creation to
     every run's ion spectrum on the host.  max_steps (for profiling) cuts
-    every run short."""
+    every run short; shapes: (unit particles, sort interval, particles per
+    thread) of the batch."""
     n_runs = len(run_ids)
     descs = [scan_desc(i, w) for i in run_ids]
     if max_steps:
         descs = [dict(d, steps=min(d["steps"], max_steps)) for d in descs]
+    shapes = shapes or w["shapes"]
     t0 = time.perf_counter()
-    b = picrr.Batch(w["cells_per_lambda"], max_runs=n_runs, cfl=w["cfl"], sort_interval=w["sort_interval"],
-                    device=device)
+    b = picrr.Batch(w["cells_per_lambda"], max_runs=n_runs, cfl=w["cfl"], sort_interval=shapes[1], device=device)
+    b.set_shapes(*shapes)
     ids = [b.add_run(d["length_lambda"], d["foil_x0"], d["foil_thickness"], d["ne"], d["a0"], d["polarization"],
                      d["duration"], d["steps"], rr_on=d["rr_on"], ppc=d["ppc"], seed=d["seed"]) for d in descs]
     while b.step(4096) > 0:
@@ -300,16 +304,19 @@ def batched_scan(picrr, device, run_ids, w=SCAN, max_steps=None):
                 push_launches=st["push_launches"], kernel_launches=st["kernel_launches"])
 
 
-def plain_scan(picrr, device, run_ids, w=SCAN):
+def plain_scan(picrr, device, run_ids, w=SCAN, shapes=None):
     """The same runs one at a time through the single-run API (create, foil,
-    laser, step to the end, ion spectrum, destroy), on the same GPU."""
+    laser, step to the end, ion spectrum, destroy), on the same GPU, with the
+    same launch shapes."""
     n_runs = len(run_ids)
     descs = [scan_desc(i, w) for i in run_ids]
+    shapes = shapes or w["shapes"]
     t0 = time.perf_counter()
     for d in descs:
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
-                      sort_interval=w["sort_interval"], seed=d["seed"], device=device)
+                      sort_interval=shapes[1], seed=d["seed"], device=device)
         s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
+        s.set_shapes(*shapes)
         s.inject_laser(d["a0"], d["polarization"], 0, d["duration"])
         s.step(d["steps"])
         s.spectra(1, 200, 0.0, 2000.0)
@@ -682,6 +689,7 @@ def main():
                          "tuner (profiling)")
     ap.add_argument("--scan-runs", type=int, default=SCAN["n_runs"], help="runs of the batched scan (0: skip)")
     ap.add_argument("--scan-steps", type=int, default=0, help="cut the scan runs to this many steps (profiling)")
+    ap.add_argument("--scan-shapes", default=None, help="UNIT,INTERVAL,PARTICLES_PER_THREAD of the scan's batch")
     ap.add_argument("--plain-runs", type=int, default=8,
                     help="runs of the scan stepped one at a time for the plain comparison (0: skip)")
     ap.add_argument("--serve-window", type=float, default=SERVE["window_s"],
@@ -692,6 +700,8 @@ def main():
                     help="arrival rate of the second (sustainable) stream; 0 skips it")
     ap.add_argument("--serve-policy", default=SERVE["policy"], choices=["sjf", "fifo"],
                     help="admission order of both serving arms: least work first, or arrival order")
+    ap.add_argument("--serve-sort-interval", type=int, default=SERVE["sort_interval"],
+                    help="sort interval of the server's batch and of the plain arm")
     ap.add_argument("--serve-resident", type=int, default=SERVE["resident"],
                     help="particles stepping at once in the server (0: no cap)")
     ap.add_argument("--preroll", type=int, default=PULSE_AT_FOIL_STEP + 82,
@@ -799,7 +809,8 @@ def main():
     traffic = None
     if shapes:
         traffic = PUSH_TRAFFIC.get((n_active, shapes["unit_particles"], shapes["sort_interval"],
-                                    shapes["particles_per_thread"], start // 100 * 100, push_kernel_digest()))
+                                    shapes["particles_per_thread"], start >= PULSE_AT_FOIL_STEP,
+                                    push_kernel_digest()))
     window = {"first_step": start, "last_step": start + args.steps - 1, "ms_raw": ms_raw, "sorts_inside": sorts_in,
               "sort_ms_inside": st1["sort_ms"], "sort_ms_mean": sort_ms_mean, "sort_interval": interval,
               "ms_with_amortised_sort": ms, "kernel_launches_before": st0["kernel_launches"],
@@ -824,9 +835,11 @@ def main():
         # whole job steps the same runs at any N)
         ranks, loads = shard(picrr, [scan_desc(i) for i in range(args.scan_runs)], ws)
         mine = [i for i, r in enumerate(ranks) if r == rank]
-        scan = batched_scan(picrr, local, mine, max_steps=args.scan_steps or None)
+        scan_shapes = tuple(int(x) for x in args.scan_shapes.split(",")) if args.scan_shapes else SCAN["shapes"]
+        scan = batched_scan(picrr, local, mine, max_steps=args.scan_steps or None, shapes=scan_shapes)
+        scan["shapes"] = scan_shapes
         if args.plain_runs > 0:
-            plain = plain_scan(picrr, local, mine[:args.plain_runs])
+            plain = plain_scan(picrr, local, mine[:args.plain_runs], shapes=scan_shapes)
             scan["plain"] = plain
             scan["speedup_runs_per_hour"] = scan["runs_per_hour"] / plain["runs_per_hour"]
         scan["workload"] = ("%d runs, 15,000 cells (30 lambda, lambda/500), 21,053 steps each; a0 U[100,600], "
@@ -852,20 +865,20 @@ def main():
             out["workload"] = ("Poisson arrivals at %g/s for %g s (seed %d), per species 1e4..1e6 particles "
                                "(log-uniform), 20..200 periods at lambda/500 in a 30-lambda box, parameters as in "
                                "the scan; 150 GB admission budget, %d slots, at most %d particles stepping at once, "
-                               "%d-step chunks, admission %s in both arms; each arm capped at %g s; latency = "
-                               "submission to ion + electron spectra on the host"
+                               "%d-step chunks, sort every %d steps, admission %s in both arms; each arm capped "
+                               "at %g s; latency = submission to ion + electron spectra on the host"
                                % (cfg["rate"], cfg["window_s"], cfg["seed"], cfg["max_runs"], cfg["resident"],
-                                  cfg["chunk"], "least work first" if cfg["policy"] == "sjf" else "in arrival order",
-                                  cfg["cap_s"]))
+                                  cfg["chunk"], cfg["sort_interval"],
+                                  "least work first" if cfg["policy"] == "sjf" else "in arrival order", cfg["cap_s"]))
             return out
 
         # one request stream split over the ranks as the requests arrive; rank 0 reports its share
         cfg = dict(SERVE, window_s=args.serve_window, cap_s=args.serve_cap, rate=args.serve_rate,
-                   policy=args.serve_policy, resident=args.serve_resident)
+                   policy=args.serve_policy, resident=args.serve_resident, sort_interval=args.serve_sort_interval)
         serving = one_stream(cfg)
         if args.serve_low_rate > 0:
             low = dict(SERVE_LOW, cap_s=args.serve_cap, rate=args.serve_low_rate, policy=args.serve_policy,
-                       resident=args.serve_resident)
+                       resident=args.serve_resident, sort_interval=args.serve_sort_interval)
             serving["sustainable_rate"] = one_stream(low)
 
     parity = None
