@@ -69,7 +69,17 @@ def test_clock_samples_are_kept_only_inside_the_timed_region(tmp_path):
 def test_both_arms_name_the_same_workload_and_traffic_is_keyed_by_shapes():
     assert "8000 ppc/species (32M e + 32M p)" in bench.large_workload()
     assert "1000 ppc/species (4M e + 4M p)" in bench.large_workload(1000)
-    # measured DRAM bytes of one push launch stay close to the 40 B per particle-step the roofline counts
-    for (n, unit, interval, w), b in bench.PUSH_TRAFFIC.items():
+    # measured DRAM bytes of one push launch stay close to the 40 B per particle-step the roofline counts,
+    # and an entry applies only to the push kernel it was measured on
+    assert any(k[5] == bench.push_kernel_digest() for k in bench.PUSH_TRAFFIC)
+    for (n, unit, interval, w, hot, digest), b in bench.PUSH_TRAFFIC.items():
         assert n == 64_000_000 and w in (2, 4) and 1 <= interval <= 64 and unit in (2048, 4096, 8192, 16384)
+        assert hot is True and len(digest) == 12
         assert 0.95 < b / (bench.BYTES_PER_PARTICLE_STEP * n) < 1.05
+
+
+def test_timed_window_follows_the_pulse():
+    """The large run's timed window starts after the pulse front reached the foil."""
+    assert bench.PULSE_AT_FOIL_STEP == 518
+    assert bench.RUN_STEPS == 2000
+    assert bench.SCAN["shapes"] == (8192, 64, 2) and bench.SERVE["sort_interval"] == 64
