@@ -316,14 +316,54 @@ def plain_scan(picrr, device, run_ids, w=SCAN, shapes=None):
         s = picrr.Sim(d["length_lambda"], w["cells_per_lambda"], cfl=w["cfl"], rr_on=d["rr_on"],
                       sort_interval=shapes[1], seed=d["seed"], device=device)
         s.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])
-        s.set_shapes(*shapes)
         s.inject_laser(d["a0"], d["polarization"], 0, d["duration"])
+        s.set_shapes(*shapes)
         s.step(d["steps"])
         s.spectra(1, 200, 0.0, 2000.0)
         s.close()
     el = time.perf_counter() - t0
     ps = sum(desc_particles(d, w["cells_per_lambda"]) * d["steps"] for d in descs)
     return dict(runs=n_runs, seconds=el, runs_per_hour=3600.0 * n_runs / el, particle_steps_per_s=ps / el)
+
+
+# thin, hot plasma: electrons with momenta of width 20 (m_e c) and cold-ish
+# protons spread uniformly over 3.84M cells (the cells of the 256-run scan),
+# about 6 particles per cell per species: the deposit's worst case, where
+# nearly every lane of a warp holds its own anchor
+THIN = dict(cells=3_840_000, per_species=22_500_000, p_e=20.0, p_i=0.05, shapes=(4096, 8, 2), warm=16, steps=24,
+            seed=1)
+
+
+def thin_leg(picrr, device, w=THIN):
+    """The push kernel on synthetic thin, hot plasma (seeded), timed with CUDA
+    events over `steps` steps after `warm`."""
+    import numpy as np
+
+    cpl = 500.0
+    s = picrr.Sim(w["cells"] / cpl, cpl, cfl=0.95, rr_on=True, sort_interval=w["shapes"][1], seed=w["seed"],
+                  device=device)
+    rng = np.random.default_rng(w["seed"])
+    n = w["per_species"]
+    cell = np.sort(rng.integers(1000, w["cells"] - 1000, n)).astype(np.int32)
+    off = rng.random(n, dtype=np.float32)
+    for sp, (ps, q, m) in enumerate([(w["p_e"], -1.0, 1.0), (w["p_i"], 1.0, 1836.15267343)]):
+        px, py, pz = (rng.standard_normal(n, dtype=np.float32) * np.float32(ps) for _ in range(3))
+        s.load_particles_f32(sp, cell, off, px, py, pz, 0.01, q, m)
+    s.set_shapes(*w["shapes"])
+    s.step(w["warm"])
+    s.set_timing(True)
+    s.step(w["steps"])
+    st = s.stats()
+    s.close()
+    push = st["push_ms"] / max(1, st["timed_push_launches"])
+    peak, kind = _peaks()
+    gbs = BYTES_PER_PARTICLE_STEP * 2 * n / (push / 1e3) / 1e9
+    return {"push_ms": push, "achieved_gbs": gbs, "frac": gbs / peak, "peak_kind": kind,
+            "field_ms": st["field_ms"] / w["steps"], "sort_ms_per_step": st["sort_ms"] / w["steps"],
+            "workload": "%d cells, %dM electrons (momenta N(0, %g)) + %dM protons (N(0, %g)) uniform, units of %d, "
+                        "sort every %d, %d per thread; %d steps timed after %d"
+                        % (w["cells"], n // 10**6, w["p_e"], n // 10**6, w["p_i"], w["shapes"][0], w["shapes"][1],
+                           w["shapes"][2], w["steps"], w["warm"])}
 
 
 def parity_leg(picrr, device):
@@ -709,6 +749,7 @@ def main():
                          "them")
     ap.add_argument("--no-rr-cost", action="store_true", help="skip the RR on/off timing after the window")
     ap.add_argument("--no-parity", action="store_true", help="skip the errors against the stored oracle results")
+    ap.add_argument("--no-thin", action="store_true", help="skip the thin, hot plasma push timing")
     ap.add_argument("--ppc", type=int, default=LARGE["ppc"],
                     help="macro-particles per cell per species (smaller values give the profiling case)")
     args = ap.parse_args()
@@ -829,6 +870,8 @@ def main():
                        "pic_set_shapes (the tuned shapes) + pic_step_n(steps 0 .. end of the timed window) + "
                        "pic_spectra + pic_energy, host wall clock"}
 
+    thin = thin_leg(picrr, local) if not args.no_thin else None
+
     scan = None
     if args.scan_runs > 0:
         # the scan's runs split over the ranks by work (strong scaling: the
@@ -915,6 +958,7 @@ def main():
             "timed_window": window,
             "rr_cost": rr_cost,
             "runs_per_hour": 3600.0 / (2000 * ms_max / args.steps / 1e3) * ws,
+            "thin_plasma": thin,
             "batched_scan": scan,
             "serving": serving,
             "e2e": e2e,
