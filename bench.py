@@ -640,7 +640,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": large_workload(), "cells": 200000},
+            "config": {"workload": workload_with_window(window_start(args.steps, args.warmup, args.preroll, 64),
+                                                        args.steps),
+                       "cells": 200000},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -665,6 +667,25 @@ def large_workload(ppc=LARGE["ppc"]):
     n = ppc * int(round(LARGE["foil_thickness"] * LARGE["cells_per_lambda"]))
     return ("large single run: 200,000 cells (100 lambda, lambda/2000), 2-lambda H foil n_e=100 n_c, "
             "%d ppc/species (%.3gM e + %.3gM p), CP a0=500, RR on" % (ppc, n / 1e6, n / 1e6))
+
+
+# steps the shape tuner takes (its trials are real steps): two particles-per-thread trials and four
+# unit-size trials at the default interval of 8, then one trial per interval of 8, 16, 32, 64; each
+# trial is one warm-up interval plus 64 steps rounded to whole intervals
+TUNER_STEPS = 6 * (8 + 64) + sum(i + max(i, 64 // i * i) for i in (8, 16, 32, 64))
+
+
+def window_start(steps, warmup, preroll, interval, tuned=True):
+    """First timed step of the large run: the last `steps` of the 2000-step
+    run when they fit after the pre-roll, the tuner, two sort intervals and
+    the warm-up; otherwise right after those."""
+    now = preroll + (TUNER_STEPS if tuned else 0)
+    return max(RUN_STEPS - steps, now + 2 * interval + warmup)
+
+
+def workload_with_window(start, steps, ppc=LARGE["ppc"]):
+    return (large_workload(ppc) + "; timed steps %d..%d of the 2000-step run (the pulse front reaches the foil at "
+            "step %d)" % (start, start + steps - 1, PULSE_AT_FOIL_STEP))
 
 
 def make_sim(picrr, device, w=LARGE):
@@ -944,9 +965,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": large_workload(args.ppc) + "; timed steps %d..%d of the 2000-step run (the "
-                                   "pulse front reaches the foil at step %d)"
-                                   % (start, start + args.steps - 1, PULSE_AT_FOIL_STEP),
+            "config": {"workload": workload_with_window(start, args.steps, args.ppc),
                        "particles": n_active, "particles_end": n_active_end, "cells": 200000,
                        "sort_interval": interval,
                        "shapes": shapes, "hot_at_window_start": hot,

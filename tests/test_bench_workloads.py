@@ -79,7 +79,12 @@ def test_both_arms_name_the_same_workload_and_traffic_is_keyed_by_shapes():
 
 
 def test_timed_window_follows_the_pulse():
-    """The large run's timed window starts after the pulse front reached the foil."""
+    """The large run's timed window starts after the pulse front reached the foil
+    and after the tuner's 808 trial steps; both arms name the same window."""
     assert bench.PULSE_AT_FOIL_STEP == 518
     assert bench.RUN_STEPS == 2000
+    assert bench.TUNER_STEPS == 808
+    assert bench.window_start(20, 5, 600, 64) == 1980 and bench.window_start(384, 8, 600, 64) == 1616
+    assert bench.window_start(1500, 5, 600, 64) == 600 + 808 + 128 + 5
+    assert "timed steps 1980..1999" in bench.workload_with_window(1980, 20)
     assert bench.SCAN["shapes"] == (8192, 64, 2) and bench.SERVE["sort_interval"] == 64
