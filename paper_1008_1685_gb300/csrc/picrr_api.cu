@@ -1110,6 +1110,10 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
     if ((st = upload_blocks(b)) != PIC_OK) return st;
     const int I = b->sort_interval;
     int64_t it = 0;
+    // laser source values of the single steps below, uploaded for up to KMAX
+    // steps at a time (one copy instead of one per step); a graph launch
+    // uploads its own interval over them
+    int inc_pos = 0, inc_len = 0;
     while (it < n) {
         int nact = 0;
         bool whole_chunk = b->graphs_on && b->since_sort == 0 && n - it >= I;
@@ -1125,6 +1129,7 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
             const int gp = static_cast<int>(b->gstep & 1), gc = b->cur;
             if ((st = chunk_graph(b, gp, gc, &ex)) != PIC_OK) return st;
             if ((st = upload_incident(b, I)) != PIC_OK) return st;
+            inc_pos = inc_len = 0;
             read_graph_timing(b, gp, gc);  // its previous launch (two chunks ago), before its events are reused
             PIC_CK(b, cudaGraphLaunch(ex, b->stream));
             b->graph_unread[gp][gc] = b->timing;
@@ -1153,14 +1158,18 @@ pic_status batch_step(Batch* b, int64_t n, int64_t* done) {
             if (e != cudaSuccess) return cuda_fail(b, e, "chunk launch");
             continue;
         }
-        if ((st = upload_incident(b, 1)) != PIC_OK) return st;
+        if (inc_pos >= inc_len) {
+            inc_len = static_cast<int>(std::min<int64_t>(n - it, KMAX));
+            inc_pos = 0;
+            if ((st = upload_incident(b, inc_len)) != PIC_OK) return st;
+        }
         {
             Timed t(b, 0);
             launch_push(push_params(b, b->gstep, b->since_sort, b->cur), b->max_units, b->slot_w, b->stream);
         }
         {
             Timed t(b, 1);
-            launch_field(field_params(b, b->gstep, 0), b->nblk, b->stream);
+            launch_field(field_params(b, b->gstep, inc_pos++), b->nblk, b->stream);
         }
         b->launches += 2;
         b->push_launches++;
