@@ -53,7 +53,7 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # kernel's source); a run that does not match every key, or a kernel changed
 # since the capture, reports null
 PUSH_TRAFFIC = {
-    (64_000_000, 16384, 64, 4, True, "c69fad8aa597"): 1_280_352_512 + 1_219_084_288,
+    (64_000_000, 16384, 64, 4, True, "2daf2be9a459"): 1_281_599_488 + 1_218_779_648,
 }
 
 

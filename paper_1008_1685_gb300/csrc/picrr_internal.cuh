@@ -42,7 +42,7 @@ constexpr int KMAX = 64;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
 constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push kernel (>= SPAN + 2 KMAX + 9)
 constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)
-constexpr int FIELD_T = 256;      // nodes per block of the Yee kernel
+constexpr int FIELD_T = 128;      // nodes per block of the Yee kernel (64..512 measured: 128 best)
 constexpr int KEY_T = 256;        // cells per block of the per-cell sort kernels
 constexpr int WAIT_LIMIT = 1 << 22;  // bounded spin on an mbarrier before reporting a timeout
 
