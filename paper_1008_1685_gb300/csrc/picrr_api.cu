@@ -522,7 +522,7 @@ size_t run_footprint_cpl(double cells_per_lambda, double length_lambda, int64_t 
     const int64_t ntiles = (Nx + TILE - 1) / TILE;
     const size_t units = static_cast<size_t>(2 * ((n + UNIT_P_MIN - 1) / UNIT_P_MIN + ntiles + 1));
     t += units * (6 * 4 + 8 + 2 * SSTR * 4) * 3 / 2;
-    t += static_cast<size_t>(Nx / FIELD_T + 1) * 8 * 3 / 2;
+    t += static_cast<size_t>(Nx / FIELD_NODES + 1) * 8 * 3 / 2;
     return t;
 }
 
@@ -879,14 +879,14 @@ pic_status upload_table(Batch* b) {
     return PIC_OK;
 }
 
-// Block table of the Yee kernel: FIELD_T nodes of one active run per block.
+// Block table of the Yee kernel: FIELD_NODES nodes of one active run per block.
 pic_status upload_blocks(Batch* b) {
     if (!b->layout_dirty) return PIC_OK;
     std::vector<int32_t> br, bi;
     for (int i = 0; i < b->max_runs; ++i) {
         const RunHost& r = b->runs[i];
         if (!r.used || !r.active) continue;
-        for (int i0 = 0; i0 <= r.Nx; i0 += FIELD_T) {
+        for (int i0 = 0; i0 <= r.Nx; i0 += FIELD_NODES) {
             br.push_back(i);
             bi.push_back(i0);
         }

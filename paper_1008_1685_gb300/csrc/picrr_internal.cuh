@@ -42,7 +42,15 @@ constexpr int KMAX = 64;          // largest sort interval
 constexpr int PUSH_T = 256;       // threads of the push kernel
 constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push kernel (>= SPAN + 2 KMAX + 9)
 constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)
-constexpr int FIELD_T = 128;      // nodes per block of the Yee kernel (64..512 measured: 128 best)
+constexpr int FIELD_T = 128;      // threads of the Yee kernel
+// Nodes per thread of the Yee kernel.  Measured per step (1 / 2 / 4 / 8): 256 runs of 15,000
+// cells 0.082 / 0.075 / 0.073 / 0.081 ms, one run of 200,000 cells 0.0102 / 0.0107 / 0.0121 /
+// 0.0144 ms (too few blocks for the SMs at 4 and 8); one node per thread with the current
+// staged through shared memory and the last loads issued after the barriers took 0.096 ms.
+#ifndef PICRR_FIELD_NPT
+#define PICRR_FIELD_NPT 2
+#endif
+constexpr int FIELD_NODES = FIELD_T * PICRR_FIELD_NPT;  // nodes per block of the Yee kernel
 constexpr int KEY_T = 256;        // cells per block of the per-cell sort kernels
 constexpr int WAIT_LIMIT = 1 << 22;  // bounded spin on an mbarrier before reporting a timeout
 

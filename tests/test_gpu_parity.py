@@ -83,6 +83,27 @@ def test_one_step_random_particles_and_fields(picrr, rr):
         assert eg[3] == pytest.approx(eo[3], rel=1e-4)
 
 
+@pytest.mark.parametrize("nx", [100, 255, 256, 257, 511, 512, 513, 1025])
+def test_one_step_fields_at_every_node_across_block_edges(picrr, nx):
+    # the Yee kernel tiles the grid into blocks of a power-of-two number of nodes that
+    # recompute their neighbours' guard values: grids just below, at and above a multiple
+    # of the block, and shorter than one block, compared node by node after one step
+    g, o = pair(picrr, length_lambda=nx / 100.0, cells_per_lambda=100, rr_on=True)
+    assert g.nx == nx
+    F = synth.random_fields(nx, scale=50.0, seed=nx)
+    for s in (g, o):
+        s.set_fields(*F)
+    for sp, (n, q, m) in enumerate([(3 * nx + 7, -1.0, 1.0), (nx + 3, 1.0, 1836.15267343)]):
+        cell, off, px, py, pz = synth.random_particles(n, 2, nx - 2, pscale=30.0 if sp == 0 else 1.0, seed=nx + sp)
+        for s in (g, o):
+            s.load_particles(sp, cell, off, px, py, pz, 0.01, q, m)
+    g.step(1)
+    o.step(1)
+    for comp in range(8):
+        a, b = g.field(comp), o.field(comp)
+        assert np.max(np.abs(a - b)) <= 4e-6 * max(np.max(np.abs(b)), 1e-30), (comp, np.argmax(np.abs(a - b)))
+
+
 @pytest.mark.parametrize("ppt", [2, 4])
 def test_one_step_dense_tiles_split_into_units(picrr, ppt):
     """Dense cells (about 250 particles each): every 64-cell tile splits into
