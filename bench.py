@@ -53,16 +53,19 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # kernel's source); a run that does not match every key, or a kernel changed
 # since the capture, reports null
 PUSH_TRAFFIC = {
-    (64_000_000, 16384, 64, 4, True, "2daf2be9a459"): 1_281_599_488 + 1_218_779_648,
+    (64_000_000, 16384, 64, 4, True, "44679031f4f0"): 1_281_764_096 + 1_218_946_048,
 }
 
 
 def push_kernel_digest():
-    """First 12 hex digits of the SHA-256 of the push kernel's source file."""
+    """First 12 hex digits of the SHA-256 of the push kernel's source: its file
+    followed by the internal header that sets its window and unit bounds."""
     import hashlib
 
-    path = os.path.join(ROOT, "paper_1008_1685_gb300", "csrc", "k_push.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+    h = hashlib.sha256()
+    for name in ("k_push.cu", "picrr_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1008_1685_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def hot_fractions(sim, w):

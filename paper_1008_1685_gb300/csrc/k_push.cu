@@ -2,13 +2,15 @@
 // + move + charge-conserving deposit (the particle part of one PIC step).
 //
 // One CTA per work unit (at most unit_p consecutive particles of one species
-// whose cells at the last sort lie in one tile, or in one group of sparse
-// tiles holding at most unit_p particles; unit_p is a shape of the batch).
+// whose cells at the last sort lie in one tile, or in one aligned group or
+// half group of sparse tiles holding at most unit_p particles; unit_p is a
+// shape of the batch).
 // Because cfl < 1 a particle moves less than one cell per step, so k steps
 // after the sort every particle of the unit lies in [lo - k, hi + k]; the CTA
 // stages the fields of the window [lo - k - 1, hi + k + 2] into shared memory
-// with one bulk TMA copy per component (completing on one mbarrier), streams
-// the particles (structure of arrays) with 128-bit evict-first loads and
+// (with 4 particles per thread: plain loads into a gather-ready layout; with 2:
+// one bulk TMA copy per component, completing on one mbarrier), streams the
+// particles (structure of arrays) with 128- or 64-bit evict-first loads and
 // stores, and accumulates the unit's current in shared memory.
 //
 // Deposit: a particle that moves from bin b (cell at x^n) to bin b + d,
@@ -79,22 +81,24 @@ __device__ __forceinline__ void lane_add(int key, const float (&v)[8], Window& w
 // One stencil record per lane (key < 0: none).  When every lane holds the
 // same anchor (dense plasma), the records are summed exactly in 32-bit fixed
 // point (|value| < 2^26 per lane, so the warp sum fits) by one integer warp
-// reduction per value and lane 0 adds the sums; otherwise every lane adds its
-// own record.  (A reduction over lanes grouped by anchor runs once per
+// reduction per value and lanes 0..7 add the eight sums (the large run's push
+// 0.463 -> 0.450 ms against eight adds by lane 0); otherwise every lane adds
+// its own record.  (A reduction over lanes grouped by anchor runs once per
 // distinct anchor, which costs more than the lanes' own atomics as soon as
 // the warp holds two.)
 __device__ __forceinline__ void warp_add(int key, const float (&v)[8], Window& w, float lscale) {
     const int k0 = __shfl_sync(FULL, key, 0);
     if (__all_sync(FULL, key == k0)) {
         if (k0 >= 0) {
-            int t[8];
+            // lane q (q < 8) adds the warp sum of value q: eight distinct words
+            const int lane = threadIdx.x & 31;
+            int mine = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) t[q] = __reduce_add_sync(FULL, __float2int_rn(v[q] * lscale));
-            if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (t[q]) win_add(w, rec_comp(q), rec_at(k0, q), t[q]);
+            for (int q = 0; q < 8; ++q) {
+                const int t = __reduce_add_sync(FULL, __float2int_rn(v[q] * lscale));
+                mine = lane == q ? t : mine;
             }
+            if (lane < 8 && mine) win_add(w, rec_comp(lane), rec_at(k0, lane), mine);
         }
     } else if (key >= 0) {
         lane_add(key, v, w, lscale);
@@ -151,12 +155,35 @@ struct Slot<2> {
     static __device__ __forceinline__ F pack(const float (&v)[2]) { return make_float2(v[0], v[1]); }
 };
 
+// Shared memory of a CTA: the unit's current window and its field window.  With
+// 4 particles per thread (dense foils, many particles per window cell) the
+// fields are read with plain loads into a layout made for the gather: per node
+// i (Ey, Ey[i+1] - Ey, Ez, Ez[i+1] - Ez) and per half node (Ex, dEx, By, dBy)
+// and (Bz, dBz), so that a particle's gather is three loads and five FMAs
+// (the large run's push 0.451 -> 0.441 ms).  With 2 per thread (thin plasma,
+// few particles per cell) the components are copied as they are by bulk TMA,
+// and the smaller footprint keeps six CTAs per SM.
+template <int W>
+struct PushSmem;
+template <>
+struct PushSmem<4> {
+    float4 nd[WMAX];
+    float4 hf[WMAX];
+    float2 hz[WMAX];
+    Window J;
+};
+template <>
+struct PushSmem<2> {
+    float F[5][WMAX];
+    Window J;
+};
+
 template <int W>
 __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(const PushParams P) {
     using I = typename Slot<W>::I;
     using F = typename Slot<W>::F;
-    __shared__ __align__(128) float sF[5][WMAX];
-    __shared__ __align__(16) Window sJ;  // the unit's current: Jx (half nodes), Jy, Jz (nodes) of the window
+    __shared__ __align__(128) PushSmem<W> sm;
+    Window& sJ = sm.J;  // the unit's current: Jx (half nodes), Jy, Jz (nodes) of the window
     __shared__ __align__(8) uint64_t bar;
     __shared__ double sred[PUSH_T / 32];
 
@@ -186,7 +213,7 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
         (&sJ.lo[0][0])[i] = 0u;
         (&sJ.hi[0][0])[i] = 0;
     }
-    if (tid == 0) {
+    if (W == 2 && tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -198,10 +225,23 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
     // each neighbouring unit in those slots are never written here
     const int base = start & ~(W - 1);
     const int npw = ((end + W - 1) & ~(W - 1)) - base;
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
+    if constexpr (W == 2) {
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&bar, 5u * static_cast<uint32_t>(L) * 4u);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) tma_load_1d(&sF[c][0], R.F[par][c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
+            for (int c = 0; c < 5; ++c)
+                tma_load_1d(&sm.F[c][0], R.F[par][c] + p0, static_cast<uint32_t>(L) * 4u, &bar);
+        }
+    } else {
+        const float* const* Fg = R.F[par];
+        for (int i = tid; i < L; i += PUSH_T) {
+            const int a = p0 + i, b = p0 + (i + 1 < L ? i + 1 : i);  // both within [p0, p1)
+            const float ey = __ldg(Fg[1] + a), ez = __ldg(Fg[2] + a), ex = __ldg(Fg[0] + a);
+            const float by = __ldg(Fg[3] + a), bz = __ldg(Fg[4] + a);
+            sm.nd[i] = make_float4(ey, __ldg(Fg[1] + b) - ey, ez, __ldg(Fg[2] + b) - ez);
+            sm.hf[i] = make_float4(ex, __ldg(Fg[0] + b) - ex, by, __ldg(Fg[3] + b) - by);
+            sm.hz[i] = make_float2(bz, __ldg(Fg[4] + b) - bz);
+        }
     }
 
     const float qm = R.qm[s], qw = R.qw[s];
@@ -216,13 +256,17 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
     const int nslots = npw / W;
     const int rounds = (nslots + PUSH_T - 1) / PUSH_T;
 
-    const bool got = mbar_wait_bounded(&bar, 0);
-    if (!__syncthreads_and(got)) {
-        if (tid == 0) {
-            atomicOr(P.status, ST_TIMEOUT);
-            mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
+    if constexpr (W == 2) {
+        const bool got = mbar_wait_bounded(&bar, 0);
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) {
+                atomicOr(P.status, ST_TIMEOUT);
+                mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
+            }
+            return;
         }
-        return;
+    } else {
+        __syncthreads();
     }
 
     const bool thin = end - start < kThinPerCell * (hi - lo + 1);  // block-uniform
@@ -279,14 +323,27 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
             float ay = 0.f, az = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, dj0 = 0.f, dj1 = 0.f;
             if (a) {
                 // --- linear gather: nodes (Ey, Ez) and half nodes (Ex, By, Bz)
-                const float e_y = (1.f - f) * sF[1][lb] + f * sF[1][lb + 1];
-                const float e_z = (1.f - f) * sF[2][lb] + f * sF[2][lb + 1];
                 const float h = f - 0.5f;
                 const int jb = h < 0.f ? lb - 1 : lb;
                 const float g = h < 0.f ? h + 1.f : h;
-                const float e_x = (1.f - g) * sF[0][jb] + g * sF[0][jb + 1];
-                const float b_y = (1.f - g) * sF[3][jb] + g * sF[3][jb + 1];
-                const float b_z = (1.f - g) * sF[4][jb] + g * sF[4][jb + 1];
+                float e_x, e_y, e_z, b_y, b_z;
+                if constexpr (W == 4) {
+                    const float4 nd = sm.nd[lb];
+                    const float4 hf = sm.hf[jb];
+                    const float2 hz = sm.hz[jb];
+                    e_y = fmaf(f, nd.y, nd.x);
+                    e_z = fmaf(f, nd.w, nd.z);
+                    e_x = fmaf(g, hf.y, hf.x);
+                    b_y = fmaf(g, hf.w, hf.z);
+                    b_z = fmaf(g, hz.y, hz.x);
+                } else {
+                    const float(*sF)[WMAX] = sm.F;
+                    e_y = (1.f - f) * sF[1][lb] + f * sF[1][lb + 1];
+                    e_z = (1.f - f) * sF[2][lb] + f * sF[2][lb + 1];
+                    e_x = (1.f - g) * sF[0][jb] + g * sF[0][jb + 1];
+                    b_y = (1.f - g) * sF[3][jb] + g * sF[3][jb + 1];
+                    b_z = (1.f - g) * sF[4][jb] + g * sF[4][jb + 1];
+                }
                 // --- Boris step for the Lorentz force (Bx = 0 in 1D)
                 const float mx = px + hq * e_x, my = py + hq * e_y, mz = pz + hq * e_z;
                 const float ig = rsqrt_ge1(1.f + mx * mx + my * my + mz * mz);

@@ -345,13 +345,19 @@ __global__ void __launch_bounds__(SCAN_T) k_tile_units(const SortParams S) {
     const int ntiles = (R.Nx + TILE - 1) / TILE;
     const int32_t* ks = R.keystart[s];
     for (int t = threadIdx.x; t < ntiles; t += SCAN_T) {
-        // a group of GROUP tiles holding at most unit_p particles is one unit,
-        // counted on its first tile; otherwise each tile is split on its own
+        // an aligned group of GROUP tiles holding at most unit_p particles is one
+        // unit, counted on its first tile; otherwise each aligned half group of
+        // GROUP / 2 tiles that holds at most unit_p is one unit; otherwise each
+        // tile is split on its own
         const int g0 = (t / GROUP) * SPAN;
         const int gn = ks[min(g0 + SPAN, R.Nx)] - ks[g0];
+        const int h0 = (t / (GROUP / 2)) * (SPAN / 2);
+        const int hn = ks[min(h0 + SPAN / 2, R.Nx)] - ks[h0];
         int n;
         if (gn <= S.unit_p) {
             n = (t % GROUP == 0 && gn > 0) ? 1 : 0;
+        } else if (hn <= S.unit_p) {
+            n = (t % (GROUP / 2) == 0 && hn > 0) ? 1 : 0;
         } else {
             const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
             n = (te - ts + S.unit_p - 1) / S.unit_p;
@@ -400,10 +406,15 @@ __global__ void k_fill_units(const SortParams S, int ubuf) {
     const int32_t* ks = R.keystart[s];
     const int g0 = (t / GROUP) * SPAN;
     const int gs = ks[g0], ge = ks[min(g0 + SPAN, R.Nx)];
+    const int h0 = (t / (GROUP / 2)) * (SPAN / 2);
+    const int hs = ks[h0], he = ks[min(h0 + SPAN / 2, R.Nx)];
     int a, b;
     if (ge - gs <= S.unit_p) {  // the whole group (t is its first tile)
         a = gs;
         b = ge;
+    } else if (he - hs <= S.unit_p) {  // the half group (t is its first tile)
+        a = hs;
+        b = he;
     } else {
         const int ts = ks[t * TILE], te = ks[min((t + 1) * TILE, R.Nx)];
         a = ts + (v - tf[t]) * S.unit_p;
