@@ -53,7 +53,7 @@ BYTES_PER_PARTICLE_STEP = 40  # cell + offset + 3 momenta, read and written (int
 # kernel's source); a run that does not match every key, or a kernel changed
 # since the capture, reports null
 PUSH_TRAFFIC = {
-    (64_000_000, 16384, 64, 4, True, "44679031f4f0"): 1_281_764_096 + 1_218_946_048,
+    (64_000_000, 16384, 96, 4, True, "992417de0ac0"): 1_282_267_392 + 1_219_133_184,
 }
 
 
@@ -114,7 +114,7 @@ def rr_cost_leg(sim, interval, reps=3):
 # 10 lambda, 40 periods each (21,053 steps), per-run parameters drawn from the run's seed
 PLAIN_SHAPES = (4096, 8, 2)  # the library's default launch shapes
 SCAN = dict(n_runs=256, length_lambda=30.0, cells_per_lambda=500.0, cfl=0.95, foil_x0=10.0, periods=40.0,
-            duration=20.0, seed_base=1000, sort_interval=8, shapes=(8192, 64, 2))
+            duration=20.0, seed_base=1000, sort_interval=8, shapes=(8192, 96, 2))
 
 
 def scan_steps(periods, w=SCAN):
@@ -643,7 +643,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_with_window(window_start(args.steps, args.warmup, args.preroll, 64),
+            "config": {"workload": workload_with_window(window_start(args.steps, args.warmup, args.preroll),
                                                         args.steps),
                        "cells": 200000},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
@@ -673,17 +673,18 @@ def large_workload(ppc=LARGE["ppc"]):
 
 
 # steps the shape tuner takes (its trials are real steps): two particles-per-thread trials and four
-# unit-size trials at the default interval of 8, then one trial per interval of 8, 16, 32, 64; each
-# trial is one warm-up interval plus 64 steps rounded to whole intervals
-TUNER_STEPS = 6 * (8 + 64) + sum(i + max(i, 64 // i * i) for i in (8, 16, 32, 64))
+# unit-size trials at the default interval of 8, then one trial per interval of 8, 16, 32, 64, 96;
+# each trial is one warm-up interval plus TUNER_TRIAL steps rounded to whole intervals (at least one)
+TUNER_TRIAL = 48
+TUNER_STEPS = 6 * (8 + TUNER_TRIAL) + sum(i + max(i, TUNER_TRIAL // i * i) for i in (8, 16, 32, 64, 96))
 
 
-def window_start(steps, warmup, preroll, interval, tuned=True):
+def window_start(steps, warmup, preroll, tuned=True):
     """First timed step of the large run: the last `steps` of the 2000-step
-    run when they fit after the pre-roll, the tuner, two sort intervals and
-    the warm-up; otherwise right after those."""
+    run when they fit after the pre-roll, the tuner and the warm-up;
+    otherwise right after those."""
     now = preroll + (TUNER_STEPS if tuned else 0)
-    return max(RUN_STEPS - steps, now + 2 * interval + warmup)
+    return max(RUN_STEPS - steps, now + warmup)
 
 
 def workload_with_window(start, steps, ppc=LARGE["ppc"]):
@@ -816,24 +817,18 @@ def main():
     # window both run with the pulse in the foil
     sim.step(args.preroll)
     if shapes is None and not args.no_tune:
-        unit, interval, ppt, tms = sim.tune_shapes(64)
+        unit, interval, ppt, tms = sim.tune_shapes(TUNER_TRIAL)
         shapes = {"unit_particles": unit, "sort_interval": interval, "particles_per_thread": ppt, "tuned": True,
                   "tuned_from_step": sim.stats()["steps"],
                   "trial_ms_per_step": {"particles_per_thread_4_2": [round(v, 4) for v in tms[:2]],
                                         "unit_2048_4096_8192_16384": [round(v, 4) for v in tms[2:6]],
-                                        "interval_8_16_32_64": [round(v, 4) for v in tms[6:]]}}
+                                        "interval_8_16_32_64_96": [round(v, 4) for v in tms[6:]]}}
     interval = shapes["sort_interval"] if shapes else w["sort_interval"]
     # the timed window ends at the run's last step (2000) when it fits after
-    # the pre-roll, the tuner, one sort interval timed for the amortised sort
-    # cost and the warm-up; otherwise it starts right after them
+    # the pre-roll, the tuner and the warm-up; otherwise it starts right after them
     now = sim.stats()["steps"]
-    start = max(RUN_STEPS - args.steps, now + 2 * interval + args.warmup)
-    sim.step(start - args.warmup - 2 * interval - now)
-    sim.set_timing(True)
-    sa = sim.stats()
-    sim.step(2 * interval)  # holds at least one whole sort (timed on the launching stream)
-    sb = sim.stats()
-    sort_ms_mean = sb["sort_ms"] / max(1, sb["sort_count"] - sa["sort_count"])
+    start = max(RUN_STEPS - args.steps, now + args.warmup)
+    sim.step(start - args.warmup - now)
     sim.step(args.warmup)
     hot = hot_fractions(sim, w)
     st0 = sim.stats()
@@ -862,9 +857,18 @@ def main():
     st1 = sim.stats()
     n_active_end = st1["active_particles"]
     # whatever sorts fell inside the K timed steps are replaced by K / interval
-    # sorts of the mean measured duration, so that the value holds the
-    # amortised sort at any K
+    # sorts of their mean measured duration (timed on the launching stream;
+    # when none fell inside, two whole intervals right after the window are
+    # timed for it), so that the value holds the amortised sort at any K
     sorts_in = st1["sort_count"] - st0["sort_count"]
+    if sorts_in > 0:
+        sort_ms_mean = st1["sort_ms"] / sorts_in
+    else:
+        sim.set_timing(True)
+        sa = sim.stats()
+        sim.step(2 * interval)
+        sb = sim.stats()
+        sort_ms_mean = sb["sort_ms"] / max(1, sb["sort_count"] - sa["sort_count"])
     ms = ms_raw - st1["sort_ms"] + args.steps * sort_ms_mean / interval
     ms_max, total = aggregate(torch, dist, ms, float(n_active) * args.steps)
     value = total / (ms_max / 1e3)

@@ -68,7 +68,7 @@ typedef struct {
     double cfl;              /* dt/dx, 0 < cfl < 1 (a particle moves < 1 cell per step) */
     double lambda_um;        /* wavelength in micrometres; sets eps = (4/3) pi r_e / lambda */
     int rr_on;               /* 1: radiation-reaction kick on electrons (Sec. 3); 0: Boris only */
-    int sort_interval;       /* steps between cell sorts, 1..64 (0 selects 8) */
+    int sort_interval;       /* steps between cell sorts, 1..96 (0 selects 8) */
     uint64_t seed;           /* seed of the foil loader's counter-based generator */
     int device;              /* CUDA device ordinal */
     int source_node;         /* node of the laser injection plane, 2..Nx-4 (0 selects 8) */
@@ -202,7 +202,7 @@ typedef struct {
 
 /* Launch shapes.  unit_particles: the most particles one CTA of the fused
  * push kernel takes (its work unit), a power of two in [1024, 16384]
- * (default 4096); sort_interval in [1, 64]; particles_per_thread: 4 or 2,
+ * (default 4096); sort_interval in [1, 96]; particles_per_thread: 4 or 2,
  * the particles each thread of the push kernel takes per round (4: 128-bit
  * loads and stores and the fewest instructions per particle, for dense foils;
  * 2: fewer registers and more warps per SM, which hides the latency of
@@ -218,9 +218,9 @@ pic_status pic_set_shapes(pic_sim* sim, int unit_particles, int sort_interval, i
  * (rounded to whole sort intervals, after one warm-up interval) with 4 and 2
  * particles per thread, keeps the faster, then at each unit size of {2048,
  * 4096, 8192, 16384}, keeps the fastest, then at each sort interval of {8, 16,
- * 32, 64}; measures the wall time per step (CUDA graphs, as pic_step_n runs
- * them) and keeps the fastest shapes.  *unit_particles, *sort_interval and
- * *particles_per_thread (nullable) receive them; ms_per_step[10] (nullable)
+ * 32, 64, 96}; measures the wall time per step (CUDA graphs, as pic_step_n
+ * runs them) and keeps the fastest shapes.  *unit_particles, *sort_interval and
+ * *particles_per_thread (nullable) receive them; ms_per_step[11] (nullable)
  * the measured times per step (particles per thread 4, 2; unit sizes;
  * intervals; -1 where not measured).  The trial steps are real steps of the
  * run.  Timing must be off. */

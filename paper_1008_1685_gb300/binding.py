@@ -427,9 +427,9 @@ class Sim:
     def tune_shapes(self, steps_per_candidate=64):
         """Pick the fastest particles per thread, work-unit size and sort interval
         by timing real steps.  Returns (unit_particles, sort_interval,
-        particles_per_thread, ms_per_step[10])."""
+        particles_per_thread, ms_per_step[11])."""
         u, c, w = C.c_int(0), C.c_int(0), C.c_int(0)
-        ms = np.full(10, -1.0)
+        ms = np.full(11, -1.0)
         self._check(self._L.pic_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c), C.byref(w),
                                             _dp(ms)))
         return u.value, c.value, w.value, ms
@@ -562,7 +562,7 @@ class Batch:
 
     def tune_shapes(self, steps_per_candidate=64):
         u, c, w = C.c_int(0), C.c_int(0), C.c_int(0)
-        ms = np.full(10, -1.0)
+        ms = np.full(11, -1.0)
         self._check(self._L.pic_batch_tune_shapes(self._h, steps_per_candidate, C.byref(u), C.byref(c),
                                                   C.byref(w), _dp(ms)))
         return u.value, c.value, w.value, ms

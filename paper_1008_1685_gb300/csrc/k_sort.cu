@@ -17,9 +17,10 @@
 //      per-warp counts combined in warp order), so the result does not depend
 //      on scheduling;
 //   4. the unit table is rebuilt from the sorted cells: tiles of TILE cells,
-//      split into chunks of at most unit_p particles, except that GROUP
-//      consecutive tiles holding at most unit_p particles together form one
-//      unit (sparse regions would otherwise give many nearly empty units).
+//      split into chunks of at most unit_p particles, except that an aligned
+//      group of GROUP consecutive tiles holding at most unit_p particles
+//      together forms one unit, or else an aligned half group that does
+//      (sparse regions would otherwise give many nearly empty units).
 // Every particle is read once and written once; the cell array is read once
 // more for the counts.
 #include <algorithm>

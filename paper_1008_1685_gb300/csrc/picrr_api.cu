@@ -353,7 +353,7 @@ pic_status validate_common(const pic_config* cfg) {
     if (!(cfg->cfl > 0.0 && cfg->cfl < 1.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "cfl must be in (0, 1)");
     if (!(cfg->lambda_um > 0.0)) return fail(nullptr, PIC_ERR_INVALID_ARG, "lambda_um must be > 0");
     if (cfg->sort_interval < 0 || cfg->sort_interval > KMAX)
-        return fail(nullptr, PIC_ERR_INVALID_ARG, "sort_interval must be in [0, 64]");
+        return fail(nullptr, PIC_ERR_INVALID_ARG, "sort_interval must be in [0, 96]");
     return PIC_OK;
 }
 
@@ -1231,7 +1231,7 @@ pic_status set_shapes(Batch* b, int unit_p, int interval, int slot_w) {
     if (unit_p < UNIT_P_MIN || unit_p > UNIT_P_MAX || (unit_p & (unit_p - 1)) != 0)
         return fail(b, PIC_ERR_INVALID_ARG, "unit size must be a power of two in [1024, 16384]");
     if (slot_w != 2 && slot_w != 4) return fail(b, PIC_ERR_INVALID_ARG, "particles per thread must be 2 or 4");
-    if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 64]");
+    if (interval < 1 || interval > KMAX) return fail(b, PIC_ERR_INVALID_ARG, "sort interval must be in [1, 96]");
     pic_status st = activate_pending(b);
     if (st != PIC_OK) return st;
     bool any = false;
@@ -1268,11 +1268,11 @@ pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval
                        double* ms_out) {
     static const int slots[2] = {4, 2};
     static const int units[4] = {2048, 4096, 8192, 16384};
-    static const int cand[4] = {8, 16, 32, 64};
+    static const int cand[5] = {8, 16, 32, 64, 96};
     if (steps_per < 1) return fail(b, PIC_ERR_INVALID_ARG, "steps_per_candidate must be >= 1");
     if (b->timing) return fail(b, PIC_ERR_STATE, "turn timing off before tuning");
     if (ms_out)
-        for (int i = 0; i < 10; ++i) ms_out[i] = -1.0;
+        for (int i = 0; i < 11; ++i) ms_out[i] = -1.0;
     auto trial = [&](int unit_p, int interval, int slot_w, double* per) -> pic_status {
         *per = -1.0;
         bool any = false;
@@ -1314,7 +1314,7 @@ pic_status tune_shapes(Batch* b, int64_t steps_per, int* unit_out, int* interval
         }
     }
     best = 1e300;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 5; ++c) {
         double per;
         if ((st = trial(best_u, cand[c], best_w, &per)) != PIC_OK) return st;
         if (ms_out) ms_out[6 + c] = per;

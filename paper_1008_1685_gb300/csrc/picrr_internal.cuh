@@ -41,7 +41,11 @@ constexpr int SPAN = GROUP * TILE;  // cell span bound of a unit
 constexpr int UNIT_P = 4096;      // default particles per unit at most (unit_p, a run-time shape of a batch)
 constexpr int UNIT_P_MIN = 1024;  // smallest unit_p (the bound used for memory estimates)
 constexpr int UNIT_P_MAX = 16384;
-constexpr int KMAX = 64;          // largest sort interval
+// Largest sort interval.  The push barely slows with the steps since the sort (+0.2 % from the first to
+// the last 8 steps of a 64-step interval), so longer intervals amortise the sort: 96 keeps the push
+// kernel's shared memory static (46 KB with 4 particles per thread); 128 needs dynamic shared memory,
+// with which the same kernel ran 1.5 % (dense) to 2.8 % (thin) slower.
+constexpr int KMAX = 96;
 constexpr int PUSH_T = 256;       // threads of the push kernel
 constexpr int WMAX = SPAN + 2 * KMAX + 16;  // window length bound in the push kernel (>= SPAN + 2 KMAX + 9)
 constexpr int SSTR = SPAN + 2 * KMAX + 4;   // per-unit key-window stride of the sort scratch (>= SPAN + 2 KMAX)

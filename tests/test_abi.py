@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_invalid_config_rejected_on_host(lib):
     import paper_1008_1685_gb300 as picrr
 
-    for bad in (dict(cfl=1.0), dict(cfl=0.0), dict(cells_per_lambda=-1.0), dict(sort_interval=65),
+    for bad in (dict(cfl=1.0), dict(cfl=0.0), dict(cells_per_lambda=-1.0), dict(sort_interval=97),
                 dict(source_node=1), dict(lambda_um=0.0)):
         kw = dict(length_lambda=4, cells_per_lambda=50, cfl=0.95)
         kw.update(bad)

@@ -73,18 +73,18 @@ def test_both_arms_name_the_same_workload_and_traffic_is_keyed_by_shapes():
     # and an entry applies only to the push kernel it was measured on
     assert any(k[5] == bench.push_kernel_digest() for k in bench.PUSH_TRAFFIC)
     for (n, unit, interval, w, hot, digest), b in bench.PUSH_TRAFFIC.items():
-        assert n == 64_000_000 and w in (2, 4) and 1 <= interval <= 64 and unit in (2048, 4096, 8192, 16384)
+        assert n == 64_000_000 and w in (2, 4) and 1 <= interval <= 96 and unit in (2048, 4096, 8192, 16384)
         assert hot is True and len(digest) == 12
         assert 0.95 < b / (bench.BYTES_PER_PARTICLE_STEP * n) < 1.05
 
 
 def test_timed_window_follows_the_pulse():
     """The large run's timed window starts after the pulse front reached the foil
-    and after the tuner's 808 trial steps; both arms name the same window."""
+    and after the tuner's 840 trial steps; both arms name the same window."""
     assert bench.PULSE_AT_FOIL_STEP == 518
     assert bench.RUN_STEPS == 2000
-    assert bench.TUNER_STEPS == 808
-    assert bench.window_start(20, 5, 600, 64) == 1980 and bench.window_start(384, 8, 600, 64) == 1616
-    assert bench.window_start(1500, 5, 600, 64) == 600 + 808 + 128 + 5
+    assert bench.TUNER_STEPS == 840
+    assert bench.window_start(20, 5, 600) == 1980 and bench.window_start(384, 8, 600) == 1616
+    assert bench.window_start(1500, 5, 600) == 600 + 840 + 5
     assert "timed steps 1980..1999" in bench.workload_with_window(1980, 20)
-    assert bench.SCAN["shapes"] == (8192, 64, 2) and bench.SERVE["sort_interval"] == 64
+    assert bench.SCAN["shapes"] == (8192, 96, 2) and bench.SERVE["sort_interval"] == 64

@@ -226,9 +226,11 @@ def test_graph_chunks_equal_single_launches(picrr):
 
 def test_shape_tuner(picrr):
     """The tuner times real steps with 4 and 2 particles per thread, then at
-    unit sizes 2048..16384, then at sort intervals 8..64, keeps the fastest
-    shapes, and the run stays on the same trajectory up to rounding."""
+    unit sizes 2048..16384, then at sort intervals 8..96, and keeps the
+    fastest shapes; its trials are ordinary steps of the run: replaying the
+    same shape changes and step counts by hand gives the same bits."""
     d = EARLY  # the pulse is in the foil from step ~50 on
+    slots, units, intervals = (4, 2), (2048, 4096, 8192, 16384), (8, 16, 32, 64, 96)
     res = []
     for tune in (True, False):
         g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
@@ -237,25 +239,37 @@ def test_shape_tuner(picrr):
         g.inject_laser(d["a0"], d["polarization"], picrr.ENV_SIN2, d["duration"])
         if tune:
             unit, interval, w, ms = g.tune_shapes(8)
-            assert unit in (2048, 4096, 8192, 16384) and interval in (8, 16, 32, 64) and w in (2, 4)
+            assert unit in units and interval in intervals and w in slots
             assert np.all(ms > 0)
-            assert w == (4, 2)[int(np.argmin(ms[:2]))] and interval == (8, 16, 32, 64)[int(np.argmin(ms[6:]))]
+            picks = (slots[int(np.argmin(ms[:2]))], units[int(np.argmin(ms[2:6]))], intervals[int(np.argmin(ms[6:]))])
+            assert (w, unit, interval) == picks
             done = g.stats()["steps"]
             # warm-up interval + trial for each candidate (a trial is at least one interval)
-            assert done == 2 * (8 + 8) + 4 * (8 + 8) + (8 + 8) + (16 + 16) + (32 + 32) + (64 + 64)
-            g.step(340 - done)
+            assert done == 2 * (8 + 8) + 4 * (8 + 8) + (8 + 8) + (16 + 16) + (32 + 32) + (64 + 64) + (96 + 96)
         else:
-            g.step(340)
-        res.append([g.field(c) for c in range(5)])
+            bw, bu, bi = picks
+            for s_ in slots:
+                g.set_shapes(4096, 8, s_)
+                g.step(16)
+            for u in units:
+                g.set_shapes(u, 8, bw)
+                g.step(16)
+            for i in intervals:
+                g.set_shapes(bu, i, bw)
+                g.step(i + max(i, 8 // i * i))
+            g.set_shapes(bu, bi, bw)
+            assert g.stats()["steps"] == done
+        g.step(640 - done)
+        res.append([g.field(c) for c in range(5)] + [g.particles(0)["px"]])
         g.close()
-    for c in range(5):
-        assert np.linalg.norm(res[0][c] - res[1][c]) <= 1e-4 * max(np.linalg.norm(res[1][c]), 1e-30), c
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
 
 
 def test_set_shapes_changes_only_rounding(picrr):
     d = EARLY
     out = []
-    for unit, interval, w in ((1024, 8, 4), (16384, 4, 2), (4096, 16, 2), (16384, 64, 4)):
+    for unit, interval, w in ((1024, 8, 4), (16384, 4, 2), (4096, 16, 2), (16384, 64, 4), (8192, 96, 2)):
         g = picrr.Sim(length_lambda=d["length_lambda"], cells_per_lambda=CPL, rr_on=d["rr_on"], sort_interval=8,
                       seed=d["seed"])
         g.load_foil(d["foil_x0"], d["foil_thickness"], d["ne"], 1, 1.0, d["ppc"])

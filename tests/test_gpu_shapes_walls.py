@@ -57,8 +57,8 @@ def two_walls(n, nx, width, pscale, seed):
     return [np.concatenate([x, y]) for x, y in zip(a, b)]
 
 
-@pytest.mark.parametrize("shapes", [(1024, 64, 2), (16384, 64, 4)])
-def test_sort_interval_64_with_particles_frozen_at_both_walls(picrr, shapes):
+@pytest.mark.parametrize("shapes", [(1024, 64, 2), (16384, 64, 4), (4096, 96, 2), (16384, 96, 4)])
+def test_long_sort_intervals_with_particles_frozen_at_both_walls(picrr, shapes):
     g, o = pair(picrr, length_lambda=2, cells_per_lambda=100)
     nx = g.nx
     for sp, (n, q, m, w, ps) in enumerate([(3001, -1.0, 1.0, 0.002, 30.0), (2999, 1.0, 1836.15267343, 0.002, 0.5)]):
@@ -68,7 +68,8 @@ def test_sort_interval_64_with_particles_frozen_at_both_walls(picrr, shapes):
     for s in (g, o):
         s.inject_laser(20.0, picrr.LP, picrr.ENV_SIN2, 1.0)
     g.set_shapes(*shapes)
-    g.step(130)  # sorts after steps 64 and 128; the pushes of steps 41..64 and 105..128 stage k >= 40
+    g.step(130)  # interval 64: sorts after steps 64 and 128 (pushes of steps 41..64 and 105..128 stage k >= 40);
+    # interval 96: one sort after step 96, windows that reach both walls from step ~90 on
     o.step(130)
     pg, po = g.particles(0), o.particles(0)
     assert np.array_equal(pg["flag"], po["flag"])
@@ -81,7 +82,7 @@ def test_sort_interval_64_with_particles_frozen_at_both_walls(picrr, shapes):
     assert np.max(np.abs(pg["x"] - po["x"])[~frozen]) <= 1e-3 * g.dx
     for comp in range(5):
         assert rel_l2(g.field(comp), o.field(comp)) <= 1e-4, comp
-    assert g.stats()["sort_count"] == 2
+    assert g.stats()["sort_count"] == 130 // shapes[1]
 
 
 FSCALE = 10.0
