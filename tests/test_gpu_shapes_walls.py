@@ -120,26 +120,29 @@ def test_tuned_shapes_dense_foil_one_step(picrr):
 
 
 def test_tuned_shapes_dense_foil_through_a_whole_sort_interval(picrr):
-    """64 steps at sort interval 64: the last push stages windows 63 steps
-    wide on each side of its units (electrons with |p| ~ 30 cross up to 60
-    cells in that time); every particle and all 8 grid components (the
-    current of step 64) against the oracle, at the tuned shapes and at the
-    default ones (units of 4096, sort every 8 steps, 2 per thread).  Over 64
-    steps the single-precision rounding grows with the dynamics: perturbing
-    the oracle's own initial momenta by 6e-8 (relative) moves them by up to
-    2e-6 and the positions by 3e-5 cells in a 200k-particle version of this
-    case, so each particle is held to 2e-4 and 1e-3 cells (a field window misplaced by even one cell changes momenta by
-    about 1e-2 in this field)."""
+    """A whole sort interval at the benchmark's shapes: 64 steps at sort
+    interval 64 and 96 steps at 96 (the last push stages windows 63 or 95
+    steps wide on each side of its units; electrons with |p| ~ 30 cross up to
+    90 cells in that time); every particle and all 8 grid components (the
+    current of the last step) against the oracle, and at the default shapes
+    (units of 4096, sort every 8 steps, 2 per thread) over 64 steps.  The
+    single-precision rounding grows with the dynamics: perturbing the oracle's
+    own initial momenta by 6e-8 (relative) moves them by up to 2e-6 and the
+    positions by 3e-5 cells over 64 steps in a 200k-particle version of this
+    case, so each particle is held to 2e-4 and 1e-3 cells (a field window
+    misplaced by even one cell changes momenta by about 1e-2 in this field)."""
     o = None
-    for shapes in ((16384, 64, 4), (4096, 8, 2)):
+    refs = {}
+    for shapes, n in (((16384, 64, 4), 64), ((4096, 8, 2), 64), ((16384, 96, 4), 96)):
         g, o2 = dense_foil_pair(picrr, shapes)
         if o is None:
             o = o2
-            o.step(64)
-            ref = [o.particles(sp) for sp in (0, 1)]
-            fref = [o.field(c) for c in range(8)]
-        g.step(64)
-        assert g.stats()["sort_count"] == 64 // shapes[1]
+        if n not in refs:
+            o.step(n - max(refs, default=0))
+            refs[n] = ([o.particles(sp) for sp in (0, 1)], [o.field(c) for c in range(8)])
+        ref, fref = refs[n]
+        g.step(n)
+        assert g.stats()["sort_count"] == n // shapes[1]
         worst = {}
         for sp in (0, 1):
             pg, po = g.particles(sp), ref[sp]
