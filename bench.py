@@ -83,6 +83,27 @@ def hot_fractions(sim, w):
     return out
 
 
+def kernel_times(sim, interval, intervals=2):
+    """Per-kernel CUDA-event times of the run's next whole sort intervals: with
+    timing on, the step graphs hold an event-record node before and after every
+    push, Yee update and sort (each pair leaves a gap of a few microseconds
+    between the kernels), so the timed window runs without them and the kernel
+    times come from these intervals of the same run, right after it."""
+    k = sim.stats()["steps_since_sort"]
+    if k:
+        sim.step(interval - k)  # to a sort boundary: whole intervals follow, as graph launches
+    s0 = sim.stats()
+    sim.set_timing(True)
+    sim.step(intervals * interval)
+    st = sim.stats()
+    sim.set_timing(False)
+    n = intervals * interval
+    return {"push_ms": st["push_ms"] / max(1, st["timed_push_launches"]), "field_ms_per_step": st["field_ms"] / n,
+            "sort_ms_mean": st["sort_ms"] / max(1, st["sort_count"] - s0["sort_count"]),
+            "steps_per_step_ms": (st["push_ms"] + st["field_ms"] + st["sort_ms"]) / n,
+            "first_step": s0["steps"], "last_step": s0["steps"] + n - 1}
+
+
 def rr_cost_leg(sim, interval, reps=3):
     """The radiation-reaction kick's cost on one state: whole sort intervals
     stepped alternately with the kick on and off (pic_set_rr), the push
@@ -841,7 +862,8 @@ def main():
     clocks = Clocks(local) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
-    sim.set_timing(True)  # counters cover the timed window only
+    sim.set_timing(False)  # no per-kernel event nodes inside the timed window (kernel_times below)
+    st0 = sim.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if clocks:
         clocks.begin()
@@ -856,23 +878,17 @@ def main():
     clk = clocks.stop() if clocks else None
     st1 = sim.stats()
     n_active_end = st1["active_particles"]
-    # whatever sorts fell inside the K timed steps are replaced by K / interval
-    # sorts of their mean measured duration (timed on the launching stream;
-    # when none fell inside, two whole intervals right after the window are
-    # timed for it), so that the value holds the amortised sort at any K
+    # kernel times (CUDA events on the launching stream) from the next two
+    # whole sort intervals; the sorts that fell inside the K timed steps are
+    # replaced by K / interval sorts of their mean duration, so that the value
+    # holds the amortised sort at any K
     sorts_in = st1["sort_count"] - st0["sort_count"]
-    if sorts_in > 0:
-        sort_ms_mean = st1["sort_ms"] / sorts_in
-    else:
-        sim.set_timing(True)
-        sa = sim.stats()
-        sim.step(2 * interval)
-        sb = sim.stats()
-        sort_ms_mean = sb["sort_ms"] / max(1, sb["sort_count"] - sa["sort_count"])
-    ms = ms_raw - st1["sort_ms"] + args.steps * sort_ms_mean / interval
+    kt = kernel_times(sim, interval)
+    sort_ms_mean = kt["sort_ms_mean"]
+    ms = ms_raw - sorts_in * sort_ms_mean + args.steps * sort_ms_mean / interval
     ms_max, total = aggregate(torch, dist, ms, float(n_active) * args.steps)
     value = total / (ms_max / 1e3)
-    push_avg_ms = st1["push_ms"] / max(1, st1["timed_push_launches"])
+    push_avg_ms = kt["push_ms"]
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_PARTICLE_STEP * n_active / (push_avg_ms / 1e3) / 1e9
     launches = st1["kernel_launches"] - st0["kernel_launches"]
@@ -882,9 +898,14 @@ def main():
                                     shapes["particles_per_thread"], start >= PULSE_AT_FOIL_STEP,
                                     push_kernel_digest()))
     window = {"first_step": start, "last_step": start + args.steps - 1, "ms_raw": ms_raw, "sorts_inside": sorts_in,
-              "sort_ms_inside": st1["sort_ms"], "sort_ms_mean": sort_ms_mean, "sort_interval": interval,
+              "sort_ms_mean": sort_ms_mean, "sort_interval": interval,
               "ms_with_amortised_sort": ms, "kernel_launches_before": st0["kernel_launches"],
-              "push_launches_before": st0["push_launches"]}
+              "push_launches_before": st0["push_launches"],
+              "kernel_times": {"first_step": kt["first_step"], "last_step": kt["last_step"],
+                               "sum_of_kernel_ms_per_step": kt["steps_per_step_ms"],
+                               "what": "per-kernel CUDA events (event-record nodes around every push, Yee update "
+                                       "and sort in the step graphs) over the two whole sort intervals after the "
+                                       "window; the window itself runs without them"}}
     rr_cost = None if args.no_rr_cost else rr_cost_leg(sim, interval)
     sim.close()
 
@@ -983,7 +1004,7 @@ def main():
                          "kernel": "k_push_deposit", "kernel_ms": push_avg_ms,
                          "peak_kind": peak_kind,
                          "bytes_per_launch": BYTES_PER_PARTICLE_STEP * n_active},
-            "step_breakdown_ms": {"push": st1["push_ms"] / args.steps, "field": st1["field_ms"] / args.steps,
+            "step_breakdown_ms": {"push": push_avg_ms, "field": kt["field_ms_per_step"],
                                   "sort_amortised": sort_ms_mean / interval},
             "timed_window": window,
             "rr_cost": rr_cost,

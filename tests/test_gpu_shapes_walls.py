@@ -127,10 +127,12 @@ def test_tuned_shapes_dense_foil_through_a_whole_sort_interval(picrr):
     current of the last step) against the oracle, and at the default shapes
     (units of 4096, sort every 8 steps, 2 per thread) over 64 steps.  The
     single-precision rounding grows with the dynamics: perturbing the oracle's
-    own initial momenta by 6e-8 (relative) moves them by up to 2e-6 and the
-    positions by 3e-5 cells over 64 steps in a 200k-particle version of this
-    case, so each particle is held to 2e-4 and 1e-3 cells (a field window
-    misplaced by even one cell changes momenta by about 1e-2 in this field)."""
+    own initial momenta by 6e-8 (relative) moves them by up to 2.1e-6 and the
+    positions by 3.3e-5 cells over 64 steps in a 200k-particle version of this
+    case (7.1e-6 and 1.5e-4 cells over 96 steps), so each particle is held to
+    2e-4 and 1e-3 cells after 64 steps and, scaled by the same growth, to 7e-4
+    and 5e-3 cells after 96 (a field window misplaced by even one cell changes
+    momenta by about 1e-2 in this field)."""
     o = None
     refs = {}
     for shapes, n in (((16384, 64, 4), 64), ((4096, 8, 2), 64), ((16384, 96, 4), 96)):
@@ -152,8 +154,9 @@ def test_tuned_shapes_dense_foil_through_a_whole_sort_interval(picrr):
         for comp in range(8):
             worst["f%d" % comp] = float(rel_l2(g.field(comp), fref[comp]))
         g.close()
-        assert worst["p0"] <= 2e-4 and worst["p1"] <= 2e-4, (shapes, worst)
-        assert worst["x0"] <= 1e-3 and worst["x1"] <= 1e-3, (shapes, worst)
+        ptol, xtol = (2e-4, 1e-3) if n == 64 else (7e-4, 5e-3)
+        assert worst["p0"] <= ptol and worst["p1"] <= ptol, (shapes, worst)
+        assert worst["x0"] <= xtol and worst["x1"] <= xtol, (shapes, worst)
         assert max(worst["f%d" % c] for c in range(8)) <= 1e-4, (shapes, worst)
 
 
