@@ -20,9 +20,9 @@ Claims checked (Sec. 4, Figs. 1-7):
 - CP, 0.3 lambda (transparency): the pulse breaks through the foil, and with
   RR the ions end with more energy (Fig. 3);
 - LP: d reaches about 1e2 at t = 1.6-1.7 T, up to four orders of magnitude
-  above CP (Fig. 4); about 20 % of the pulse energy is radiated (here 16 %,
-  see the module constants) during an interaction of about 22 cycles with RR
-  against about 30 without (Fig. 6); the missing final ion energy is of the
+  above CP (Fig. 4); roughly a fifth of the pulse energy goes into radiation
+  (here 16 %, see the module constants) while the foil takes energy for ~22
+  laser periods with RR and ~30 without (Fig. 6); the missing final ion energy is of the
   order of the radiated energy; at 12 T the spectrum with RR has a lower
   bulk energy and a smaller spread (Fig. 5); at 46 T the hot electrons of LP
   have broadened the ion spectrum far more than for CP (Fig. 7).
@@ -148,7 +148,7 @@ def test_lp_radiated_fraction(runs):
 
 
 def test_lp_interaction_time(runs):
-    """Fig. 6: the interaction lasts about 22 cycles with RR and 30 without.
+    """Fig. 6: the foil takes energy for ~22 laser periods with RR, ~30 without.
     Read here as the time at which the energy taken by the particles
     (kinetic + radiated) reaches 95 % of its final value."""
     t_rr = np.mean([r["t95"] for r in group(runs, "LP1", True)])
