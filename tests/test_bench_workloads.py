@@ -90,3 +90,46 @@ def test_timed_window_follows_the_pulse():
     assert bench.window_start(1500, 5, 600) == 600 + 840 + 5
     assert "timed steps 1980..1999" in bench.workload_with_window(1980, 20)
     assert bench.SCAN["shapes"] == (8192, 96, 2) and bench.SERVE["sort_interval"] == 64
+
+
+class _FakeSim:
+    """Steps, sorts and timing counters as the library keeps them (a sort after
+    every `interval` steps; with timing on, fixed per-kernel times)."""
+
+    def __init__(self, steps, interval, push=0.4, field=0.01, sort=0.7):
+        self.steps, self.interval, self.timing = steps, interval, False
+        self.push, self.field, self.sort = push, field, sort
+        self.sorts = steps // interval
+        self.c = dict(push_ms=0.0, field_ms=0.0, sort_ms=0.0, timed_push_launches=0)
+
+    def set_timing(self, on):
+        self.timing = bool(on)
+        if on:
+            self.c = dict(push_ms=0.0, field_ms=0.0, sort_ms=0.0, timed_push_launches=0)
+
+    def step(self, n):
+        for _ in range(n):
+            self.steps += 1
+            if self.timing:
+                self.c["push_ms"] += self.push
+                self.c["field_ms"] += self.field
+                self.c["timed_push_launches"] += 1
+            if self.steps % self.interval == 0:
+                self.sorts += 1
+                if self.timing:
+                    self.c["sort_ms"] += self.sort
+
+    def stats(self):
+        return dict(self.c, steps=self.steps, sort_count=self.sorts, steps_since_sort=self.steps % self.interval)
+
+
+def test_kernel_times_cover_whole_sort_intervals_after_the_window():
+    s = _FakeSim(2000, 96)
+    kt = bench.kernel_times(s, 96)
+    assert (kt["first_step"], kt["last_step"]) == (2016, 2207)  # to the next sort, then two whole intervals
+    assert abs(kt["push_ms"] - 0.4) < 1e-12 and abs(kt["field_ms_per_step"] - 0.01) < 1e-12
+    assert abs(kt["sort_ms_mean"] - 0.7) < 1e-12
+    assert abs(kt["steps_per_step_ms"] - (0.41 + 0.7 / 96)) < 1e-12
+    assert not s.timing  # the window's step graphs hold no event nodes afterwards
+    s = _FakeSim(1920, 64)  # already on a sort boundary
+    assert bench.kernel_times(s, 64)["first_step"] == 1920
