@@ -68,12 +68,12 @@ __device__ __forceinline__ void win_add(Window& w, int comp, int at, int t) {
 __device__ __forceinline__ int rec_comp(int q) { return q < 3 ? 1 : (q < 6 ? 2 : 0); }
 __device__ __forceinline__ int rec_at(int key, int q) { return key + (q < 3 ? q : (q < 6 ? q - 3 : q - 6)); }
 
-// One lane's record added by itself: each nonzero value in 32-bit fixed
-// point (2^lscale units, |value| < 2^26).
-__device__ __forceinline__ void lane_add(int key, const float (&v)[8], Window& w, float lscale) {
+// One lane's record added by itself: each nonzero value rounded to 32-bit
+// fixed point (records are kept in the window's units, |value| < 2^26).
+__device__ __forceinline__ void lane_add(int key, const float (&v)[8], Window& w) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const int t = __float2int_rn(v[q] * lscale);
+        const int t = __float2int_rn(v[q]);
         if (t) win_add(w, rec_comp(q), rec_at(key, q), t);
     }
 }
@@ -86,7 +86,7 @@ __device__ __forceinline__ void lane_add(int key, const float (&v)[8], Window& w
 // its own record.  (A reduction over lanes grouped by anchor runs once per
 // distinct anchor, which costs more than the lanes' own atomics as soon as
 // the warp holds two.)
-__device__ __forceinline__ void warp_add(int key, const float (&v)[8], Window& w, float lscale) {
+__device__ __forceinline__ void warp_add(int key, const float (&v)[8], Window& w) {
     const int k0 = __shfl_sync(FULL, key, 0);
     if (__all_sync(FULL, key == k0)) {
         if (k0 >= 0) {
@@ -95,13 +95,13 @@ __device__ __forceinline__ void warp_add(int key, const float (&v)[8], Window& w
             int mine = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int t = __reduce_add_sync(FULL, __float2int_rn(v[q] * lscale));
+                const int t = __reduce_add_sync(FULL, __float2int_rn(v[q]));
                 mine = lane == q ? t : mine;
             }
             if (lane < 8 && mine) win_add(w, rec_comp(lane), rec_at(k0, lane), mine);
         }
     } else if (key >= 0) {
-        lane_add(key, v, w, lscale);
+        lane_add(key, v, w);
     }
 }
 
@@ -251,8 +251,10 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
     const bool rr = s == 0 && R.rr != 0;
     const int Nx = R.Nx;
     const float hq = 0.5f * qm * dt;
-    const float jxf = qw / cfl;  // q w dx / dt
-    const float hqw = 0.5f * qw;
+    // the record's factors carry the window's power-of-two scale, so that records
+    // are summed in its units (an exact scaling: the same bits as scaling each sum)
+    const float jxf = qw / cfl * lscale;  // q w dx / dt
+    const float hqw = 0.5f * qw * lscale;
     const int nslots = npw / W;
     const int rounds = (nslots + PUSH_T - 1) / PUSH_T;
 
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
                     w0 = s0a + s0b;
                     w2 = s2a + s2b;
                     w1 = (2.f - w0) - w2;
-                    const float hqi = hqw * ign;  // (q w / 2) / gamma: ay = that times p_y
+                    const float hqi = hqw * ign;  // (q w / 2) / gamma in the window's units: ay = that times p_y
                     ay = hqi * py;
                     az = hqi * pz;
                     dj0 = s0a - s0b;
@@ -443,12 +445,12 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
             const bool merge = ka < 0 || rk < 0 || ka == rk;
             if (thin || W == 2) {
                 if (!merge) {
-                    lane_add(rk, rv, sJ, lscale);
+                    lane_add(rk, rv, sJ);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) rv[q] = 0.f;
                 }
             } else if (__any_sync(FULL, !merge)) {
-                warp_add(merge ? -1 : rk, rv, sJ, lscale);
+                warp_add(merge ? -1 : rk, rv, sJ);
                 if (!merge) {
                     rk = -1;
 #pragma unroll
@@ -474,9 +476,9 @@ __global__ void __launch_bounds__(PUSH_T, Slot<W>::MIN_BLOCKS) k_push_deposit(co
             qz[j] = pz;
         }
         if (thin) {
-            if (rk >= 0) lane_add(rk, rv, sJ, lscale);
+            if (rk >= 0) lane_add(rk, rv, sJ);
         } else {
-            warp_add(rk, rv, sJ, lscale);
+            warp_add(rk, rv, sJ);
         }
         rk = -1;
 #pragma unroll
